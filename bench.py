@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""CPR benchmark: DOF-stage updates/s of the SSP-RK3 CPR solver on GB300.
+
+Workload (one bench "step" = one whole solve): the 2D Euler isentropic vortex
+(gamma 1.4, strength 5, centred at (5, 5), mean flow (1, 1)) on the periodic
+box [0,10]^2 with 128 x 128 elements, CPR p = 3 (16 Gauss points per element,
+4 conserved variables), Rusanov flux, g_DG correction, SSP-RK3 with device-side
+CFL steps (CFL 0.08) to t = 10.  The headline value is the FP32 path; the FP64
+path runs the same solve once and both report their L2 error of the density
+averages against the exact solution (which at t = 10 equals the initial field).
+
+    value = 128 * 128 * 16 * 3 * (RK3 steps) * K / (sum of the K solve times)
+
+summed over ranks (each rank solves its own replica; no data-path collective).
+L2 is flushed (a 256 MiB write) before every timed solve, outside its events.
+The roofline object covers the dominant kernel (the fused residual + RK stage
+kernel): algorithmic bytes per launch (read q_s, read q^n in stages 2-3, write
+the stage result: 8/3 * 4 variables * 4 B per point on average) over its mean
+launch duration; a second roofline block repeats this on a 1024 x 1024 vortex
+whose state (268 MB per array) is larger than L2.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "CPR DOF-stage updates/s (FP32 vs FP64, equal L2 error) and % HBM roofline"
+UNIT = "DOF-stage/s"
+NX, P, L, EPS, T_END, CFL = 128, 3, 10.0, 5.0, 10.0, 0.08
+HBM_NX, HBM_STEPS = 1024, 20
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["cpr", "reference"], default="cpr")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def exact_rho_averages(nx):
+    """Density averages of the exact solution at t = 10 (= the initial vortex):
+    10 x 10 Gauss-Legendre rule on every element."""
+    from paper_1709_01619_gb300 import inputs
+    g, w = np.polynomial.legendre.leggauss(10)
+    h = L / nx
+    ii, jj = np.meshgrid(np.arange(nx), np.arange(nx))  # [j, i]
+    xs = (ii.ravel()[:, None] + 0.5 * (g[None, :] + 1.0)) * h          # [e, a]
+    ys = (jj.ravel()[:, None] + 0.5 * (g[None, :] + 1.0)) * h          # [e, b]
+    X = np.repeat(xs[:, None, :], 10, axis=1).reshape(nx * nx, 100)
+    Y = np.repeat(ys[:, :, None], 10, axis=2).reshape(nx * nx, 100)
+    W = (0.25 * w[:, None] * w[None, :]).reshape(100)                  # [b, a]
+    rho = inputs.vortex(X, Y, eps=EPS)[0]
+    return rho @ W
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# oracle on the host cores (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(target_s=12.0):
+    """Time the FP64 oracle on the 128^2 p=3 vortex for a bounded number of
+    SSP-RK3 steps (about target_s seconds).  Returns (DOF-stage/s, steps, s,
+    threads)."""
+    import oracle
+    from paper_1709_01619_gb300 import inputs
+    o = oracle.Config(eqn=oracle.EULER, nx=NX, ny=NX, p=P, x1=L, y1=L, cfl=CFL)
+    x, y = oracle.point_coords(o)
+    q = inputs.vortex(x, y, eps=EPS)
+    t0 = time.perf_counter()
+    q, _, _ = oracle.run(o, q, 1)
+    t1 = time.perf_counter() - t0
+    steps = int(max(1, min(400, target_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.run(o, q, steps)
+    dt = time.perf_counter() - t0
+    dof = NX * NX * (P + 1) ** 2
+    return dof * 3 * steps / dt, steps, dt, oracle.threads()
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    per_step_target = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(per_step_target)
+    vals, secs, nsteps = [], 0.0, 0
+    threads = 1
+    for _ in range(args.steps):
+        v, s, dt, threads = oracle_sample(per_step_target)
+        vals.append(v)
+        secs += dt
+        nsteps += s
+    dof = NX * NX * (P + 1) ** 2
+    value = dof * 3 * nsteps / secs
+    sample = (f"{nsteps} SSP-RK3 steps of the 128x128 p=3 vortex in FP64 over {args.steps} samples "
+              f"(the full solve to t=10 is about 5400 steps)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "euler_vortex_128x128_p3_t10", "nx": NX, "ny": NX, "p": P,
+                   "t_end": T_END, "cfl": CFL, "precision": "fp64", "l2_flush": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# CUDA path
+# ---------------------------------------------------------------------------
+def run_cpr(args, world, rank, local):
+    import torch
+    from paper_1709_01619_gb300 import _native as nat
+    from paper_1709_01619_gb300 import inputs
+
+    dof = NX * NX * (P + 1) ** 2
+    peak, peak_kind = peaks()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def make(dtype, nx=NX):
+        cfg = nat.Config(eqn=nat.EULER, nx=nx, ny=nx, p=P, x1=L, y1=L, cfl=CFL, dtype=dtype)
+        ctx = nat.Context(cfg)
+        x, y = ctx.point_coords()
+        q0 = torch.tensor(inputs.vortex(x, y, eps=EPS), dtype=cfg.torch_dtype, device="cuda")
+        return cfg, ctx, q0
+
+    def solve(ctx, q, q0, nsteps, ev=None):
+        flush.zero_()
+        q.copy_(q0)
+        ctx.set_time(0.0, 0)
+        if ev:
+            ev[0].record()
+        ctx.step(q, nsteps, 0.0, T_END)
+        if ev:
+            ev[1].record()
+
+    # ---- FP32 (headline) ----------------------------------------------------
+    cfg32, ctx32, q0_32 = make(nat.F32)
+    q32 = torch.empty_like(q0_32)
+    solve(ctx32, q32, q0_32, 20000)
+    nsteps = ctx32.get_time()[1]
+    for _ in range(max(0, args.warmup - 1)):
+        solve(ctx32, q32, q0_32, nsteps)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        solve(ctx32, q32, q0_32, nsteps, evs[k])
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    t_fin, steps_fin = ctx32.get_time()
+    ms_max = max_over_ranks(ms, world)
+    updates = dof * 3 * nsteps * args.steps
+    value = sum_over_ranks(updates, world) / (ms_max * 1e-3)
+    avg32 = ctx32.averages(q32)[0].double().cpu().numpy()
+
+    # dominant kernel: fused residual + stage, 3 launches per RK3 step
+    launch_ms = ms / (args.steps * 3 * nsteps)
+    bytes_per_launch = dof * 4 * 4 * (8.0 / 3.0)
+    achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
+
+    # ---- e2e through the host-buffer entry point ------------------------------
+    qh_in = q0_32.cpu().pin_memory()
+    qh_out = torch.empty_like(qh_in).pin_memory()
+    ctx32.set_time(0.0, 0)
+    ctx32.step_host(qh_in, qh_out, nsteps, 0.0, T_END)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx32.set_time(0.0, 0)
+        ctx32.step_host(qh_in, qh_out, nsteps, 0.0, T_END)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = sum_over_ranks(updates, world) / e2e_s
+    state_bytes = qh_in.numel() * 4
+
+    # ---- FP64 path, same solve ----------------------------------------------
+    cfg64, ctx64, q0_64 = make(nat.F64)
+    q64 = torch.empty_like(q0_64)
+    solve(ctx64, q64, q0_64, nsteps + 100)
+    n64 = ctx64.get_time()[1]
+    ev64 = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    solve(ctx64, q64, q0_64, n64, ev64)
+    torch.cuda.synchronize()
+    ms64 = ev64[0].elapsed_time(ev64[1])
+    avg64 = ctx64.averages(q64)[0].cpu().numpy()
+    exact = exact_rho_averages(NX)
+    err32 = float(np.sqrt(np.mean((avg32 - exact) ** 2)))
+    err64 = float(np.sqrt(np.mean((avg64 - exact) ** 2)))
+    diff = float(np.linalg.norm(q32.double().cpu().numpy() - q64.cpu().numpy()) /
+                 np.linalg.norm(q64.cpu().numpy()))
+    value64 = dof * 3 * n64 / (ms64 * 1e-3)
+    del ctx64
+
+    # ---- HBM-sized case: 1024^2 p=3 FP32, stage kernels timed back to back ----
+    cfgH, ctxH, q0H = make(nat.F32, HBM_NX)
+    qH = q0H.clone()
+    ctxH.step(qH, 3, 1e-4)
+    torch.cuda.synchronize()
+    eh = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    eh[0].record()
+    ctxH.step(qH, HBM_STEPS, 1e-4)
+    eh[1].record()
+    torch.cuda.synchronize()
+    msH = eh[0].elapsed_time(eh[1])
+    dofH = HBM_NX * HBM_NX * (P + 1) ** 2
+    launchH = msH / (3 * HBM_STEPS)
+    achievedH = dofH * 16 * (8.0 / 3.0) / (launchH * 1e-3) / 1e9
+    del ctxH, qH, q0H
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, s, secs, thr = oracle_sample(12.0)
+        cpu = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"{s} FP64 SSP-RK3 steps of the same 128x128 p=3 vortex ({secs:.1f} s)"}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "euler_vortex_128x128_p3_t10", "nx": NX, "ny": NX, "p": P,
+                   "points": "gauss", "flux": "rusanov", "t_end": T_END, "cfl": CFL,
+                   "rk3_steps_per_solve": nsteps, "t_reached": t_fin,
+                   "l2_flush": "256 MiB write before every timed solve",
+                   "replicas": world},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                     "kernel": "cpr_stage_kernel<float,3,Euler,LP,Rusanov>",
+                     "note": "state (4.2 MB) is L2-resident at this size"},
+        "roofline_hbm_case": {"workload": "euler_vortex_1024x1024_p3_fp32", "bound": "hbm",
+                              "achieved": achievedH, "peak": peak, "unit": "GB/s",
+                              "frac": achievedH / peak, "launch_ms": launchH,
+                              "dof_stage_per_s": dofH * 3 * HBM_STEPS / (msH * 1e-3)},
+        "f64": {"value": value64, "unit": UNIT, "ms_per_solve": ms64, "rk3_steps": n64,
+                "bound": "alu"},
+        "l2_rho_avg_error": {"f32": err32, "f64": err64},
+        "f32_vs_f64_rel_l2": diff,
+        "speedup_f32_over_f64": value / world / value64 if value64 > 0 else None,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                "d2h_bytes_per_step": state_bytes},
+        "gpu_launches": args.steps * (3 * nsteps + 2),
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_cpr(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

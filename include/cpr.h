@@ -1,0 +1,210 @@
+/*
+ * cpr.h -- C ABI of libcpr.so, the GB300 (sm_103a) CUDA implementation of the
+ * Correction Procedure via Reconstruction (CPR) hot path of Zimmerman, Regele
+ * & Wie, "A Comparative Study of 2D Numerical Methods with GPU Computing"
+ * (arXiv 1709.01619): the CPR semi-discrete residual for 2D linear advection
+ * and the compressible Euler equations on structured quadrilateral elements
+ * (Sec. 2.2, Eq. 16-17), advanced by three-stage SSP Runge-Kutta with a CFL
+ * time step (Sec. 4, Eq. 36), with the troubled-cell minmod/TVB limiter for
+ * discontinuous flows (Sec. 2.6, Eq. 35, Algorithms 10-11).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * State layout ("element-major structure of arrays"): a contiguous array of
+ * V * nx * ny * (p+1)^2 values of the configured dtype,
+ *     q[v][e][b*(p+1) + a],   e = j*nx + i,
+ * v the variable (V = 1 for advection; V = 4 for Euler with the conserved
+ * variables (rho, rho u, rho v, e) of Sec. 2 Eq. 3), (i, j) the element, a the
+ * solution point along x and b along y.  Solution points on the reference
+ * element [-1,1]^2 are the tensor product of Gauss-Legendre (default) or
+ * Gauss-Lobatto (the paper's choice, Sec. 2.2 and Fig. 1b) points.
+ *
+ * Ownership: the caller owns every state buffer it passes (device memory of
+ * the context's device, at least 16-byte aligned -- cudaMalloc and the
+ * PyTorch caching allocator give 256 -- never aliasing one another unless
+ * stated; a misaligned array is rejected with CPR_EINVAL).  The
+ * context owns its operator tables, stage scratch buffers, reduction buffers,
+ * CUDA graphs and the simulated time.
+ *
+ * Streams: all device work of a context is issued on the stream given to
+ * cpr_init (NULL = the legacy default stream), in call order.  Calls return
+ * once the work is enqueued, except cpr_norms, cpr_get_marks, cpr_get_time
+ * and cpr_step_host, which synchronise that stream.  Asynchronous CUDA errors
+ * surface as CPR_ECUDA at the next synchronising call.
+ *
+ * Errors: every call returns a cpr_status; nothing is thrown across the ABI.
+ * Invalid arguments (NULL pointers, sizes, unsupported option combinations)
+ * return CPR_EINVAL before any launch.  cpr_last_error gives a message.
+ */
+#ifndef CPR_H
+#define CPR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CPR_OK = 0,
+    CPR_EINVAL = 1,    /* bad argument or unsupported option combination */
+    CPR_ENOMEM = 2,    /* device or host allocation failed                */
+    CPR_ECUDA = 3,     /* a CUDA runtime call or a kernel failed          */
+    CPR_ENONPHYS = 4,  /* state holds rho <= 0, p <= 0 or a non-finite value */
+    CPR_ETIMEOUT = 5,  /* a bounded device wait gave up                   */
+    CPR_ENOTIMPL = 6   /* option recognised but not built                 */
+} cpr_status;
+
+enum { CPR_ADVECTION = 0, CPR_EULER = 1 };                       /* cpr_config.eqn  */
+enum { CPR_PTS_GAUSS = 0, CPR_PTS_LOBATTO = 1 };                 /* .pts            */
+enum { CPR_CORR_GDG = 0 };                                       /* .corr (Radau)   */
+enum { CPR_FLUX_RUSANOV = 0, CPR_FLUX_UPWIND = 1, CPR_FLUX_ROE = 2 }; /* .flux      */
+enum { CPR_DIV_LP = 0, CPR_DIV_CHAIN = 1 };                      /* .div            */
+enum { CPR_BC_PERIODIC = 0, CPR_BC_TRANSMISSIVE = 1 };           /* .bc_x, .bc_y    */
+enum { CPR_F64 = 0, CPR_F32 = 1 };                               /* .dtype          */
+
+/* Problem and scheme description.
+ *   eqn      CPR_ADVECTION (u_t + ax u_x + ay u_y = 0) or CPR_EULER (Sec. 2).
+ *   nx, ny   elements in x and y, each >= 1.
+ *   x0..y1   rectangular domain, x1 > x0, y1 > y0; uniform elements.
+ *   p        polynomial order, 1 <= p <= 4 (p+1 points per direction).
+ *   pts      solution points: Gauss-Legendre or Gauss-Lobatto.
+ *   corr     correction function: g_DG, the Radau polynomials (Sec. 2.2).
+ *   flux     common flux: Rusanov (Sec. 4) for both equations, exact upwind
+ *            for advection; CPR_FLUX_ROE returns CPR_ENOTIMPL.
+ *   div      flux divergence: CPR_DIV_LP differentiates the Lagrange
+ *            interpolant of the flux; CPR_DIV_CHAIN is the paper's chain rule
+ *            A(q) dq/dxi (Sec. 2.2).
+ *   ax, ay   advection velocity; gamma ratio of specific heats (Euler).
+ *   bc_x/y   periodic or transmissive (ghost state = interior edge state).
+ *   limiter  1: troubled-cell limiter on every stage result and in
+ *            cpr_limit; tvb_M is the TVB constant M (0: plain minmod) and
+ *            lim_eps the marking threshold (the paper uses 1e-3).
+ *   dtype    arithmetic and storage type of the state: CPR_F64 or CPR_F32.
+ *            Reductions and simulated time are FP64 in both.
+ *   cfl      CFL number of the time step dt = cfl * min(hx, hy) / max_speed
+ *            (Sec. 4, Eq. 36), max_speed = max over points of |u| + c. */
+typedef struct {
+    int eqn;
+    int nx, ny;
+    double x0, x1, y0, y1;
+    int p;
+    int pts;
+    int corr;
+    int flux;
+    int div;
+    double ax, ay, gamma;
+    int bc_x, bc_y;
+    int limiter;
+    double tvb_M, lim_eps;
+    int dtype;
+    double cfl;
+} cpr_config;
+
+/* Results of cpr_norms (all FP64).
+ *   sum_avg[v]  sum over elements of the element average of variable v
+ *               (Algorithm 9; conserved to round-off on periodic grids);
+ *   l2_abs/rel  ||q - q_ref||_2 and ||q - q_ref||_2 / ||q_ref||_2 over all
+ *               values (0 when no reference is given);
+ *   max_wave    max over points of |u| + c (|a| for advection);
+ *   n_nonphys   points with rho <= 0, p <= 0 or a non-finite value;
+ *   n_marked    elements marked by the most recent limiter pass;
+ *   t, steps    simulated time and RK3 steps taken by this context. */
+typedef struct {
+    double sum_avg[4];
+    double l2_abs, l2_rel;
+    double max_wave;
+    long long n_nonphys;
+    long long n_marked;
+    double t;
+    long long steps;
+} cpr_norms_out;
+
+typedef struct cpr_ctx cpr_ctx;
+
+/* Create a context on the current CUDA device.  Validates *cfg (CPR_EINVAL),
+ * builds the operator tables on the host in FP64, allocates the stage
+ * scratch (two state-sized buffers), reduction buffers and the control
+ * block, and sets the simulated time to 0.  stream is a cudaStream_t (may be
+ * NULL).  On failure *out is NULL. */
+cpr_status cpr_init(const cpr_config* cfg, void* stream, cpr_ctx** out);
+
+/* Release everything the context owns (NULL is accepted). */
+void cpr_destroy(cpr_ctx* ctx);
+
+/* Number of values in one state array: V * nx * ny * (p+1)^2. */
+size_t cpr_state_elems(const cpr_ctx* ctx);
+
+/* Message of the last failed call on ctx (or of the last failed cpr_init when
+ * ctx is NULL).  Valid until the next call on the same context. */
+const char* cpr_last_error(const cpr_ctx* ctx);
+
+/* Physical coordinates of every solution point, host arrays of
+ * nx*ny*(p+1)^2 doubles each, layout x[e][b*(p+1) + a] (the affine map of
+ * the standard element, Sec. 2). */
+cpr_status cpr_point_coords(const cpr_ctx* ctx, double* x_host, double* y_host);
+
+/* r = R(q), the CPR right-hand side dq/dt = -(Pi[div F] + delta) at every
+ * solution point (Sec. 2.2, Eq. 16-17), with the common flux of cfg.flux on
+ * every face.  q_dev and r_dev: device state arrays; must not alias. */
+cpr_status cpr_residual(cpr_ctx* ctx, const void* q_dev, void* r_dev);
+
+/* Advance q_dev in place by up to nsteps SSP-RK3 steps (Sec. 4):
+ *   q1 = q + dt R(q);  q2 = 3/4 q + 1/4 (q1 + dt R(q1));
+ *   q  = 1/3 q + 2/3 (q2 + dt R(q2)),
+ * applying the limiter to q1, q2 and q when cfg.limiter is set.
+ * dt_fixed > 0: every step uses dt_fixed.  dt_fixed <= 0: each step uses the
+ * CFL step of the state at its start, computed on the device.
+ * t_end > 0: no step goes past simulated time t_end; the step that reaches
+ * it is shortened to land on t_end and the remaining steps do no work.
+ * The simulated time and step count advance on the device, so consecutive
+ * steps need no host synchronisation; the RK loop runs as CUDA graph
+ * replays. */
+cpr_status cpr_step(cpr_ctx* ctx, void* q_dev, int nsteps, double dt_fixed, double t_end);
+
+/* Same as cpr_step for a state held in HOST memory: copies q_in_host to the
+ * device, steps, copies the result to q_out_host (may equal q_in_host) and
+ * synchronises.  Pinned host memory gives the fastest copies.  The device
+ * state lives in a context-owned buffer allocated on first use. */
+cpr_status cpr_step_host(cpr_ctx* ctx, const void* q_in_host, void* q_out_host, int nsteps,
+                         double dt_fixed, double t_end);
+
+/* Apply the troubled-cell limiter once to q_dev in place (Sec. 2.6 Eq. 35,
+ * Algorithms 10-11): an element is marked when, at any edge point and for
+ * any variable, |delta - mt(delta, D+, D-)| > lim_eps, where delta is the
+ * outward deviation of the edge value from the element average, D+/D- the
+ * differences of neighbouring averages across that edge, and mt the TVB
+ * minmod; marked elements become qbar + (x - x0) mm(Dx+/hx, Dx-/hx)
+ * + (y - y0) mm(Dy+/hy, Dy-/hy).  Works whether or not cfg.limiter is set. */
+cpr_status cpr_limit(cpr_ctx* ctx, void* q_dev);
+
+/* Marks of the most recent limiter pass: marks_host[e] = 1 for limited
+ * elements (nx*ny ints).  Synchronises. */
+cpr_status cpr_get_marks(cpr_ctx* ctx, int* marks_host);
+
+/* Element averages of q_dev (Algorithm 9): avg_dev[v][e] = sum over points of
+ * (w_a w_b / 4) q[v][e][b*n+a], V*nx*ny values of the state dtype. */
+cpr_status cpr_averages(cpr_ctx* ctx, const void* q_dev, void* avg_dev);
+
+/* FP64 norms of q_dev (q_ref_dev nullable), see cpr_norms_out; deterministic
+ * (fixed reduction order).  Synchronises.  Returns CPR_ENONPHYS (with *out
+ * filled) when n_nonphys > 0. */
+cpr_status cpr_norms(cpr_ctx* ctx, const void* q_dev, const void* q_ref_dev, cpr_norms_out* out);
+
+/* Simulated time and step counter of the context. */
+cpr_status cpr_set_time(cpr_ctx* ctx, double t, long long steps);
+cpr_status cpr_get_time(cpr_ctx* ctx, double* t, long long* steps);
+
+/* Discrete adjoint (smooth, unlimited, LP divergence):
+ * cpr_residual_vjp: qbar = (dR/dq)^T rbar at state q.
+ * cpr_step_vjp: qbar_in = (dq_{n+1}/dq_n)^T qbar_out for one SSP-RK3 step of
+ * size dt from state q_dev (stages recomputed internally).
+ * All arguments are device state arrays that must not alias. */
+cpr_status cpr_residual_vjp(cpr_ctx* ctx, const void* q_dev, const void* rbar_dev, void* qbar_dev);
+cpr_status cpr_step_vjp(cpr_ctx* ctx, const void* q_dev, const void* qbar_out_dev, void* qbar_in_dev,
+                        double dt);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CPR_H */

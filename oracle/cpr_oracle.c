@@ -1073,14 +1073,18 @@ long oracle_run(const oracle_cfg* c, double* q, long nsteps, double dt, double t
     long taken = 0;
     double tt = t ? *t : 0.0;
     for (long s = 0; s < nsteps; ++s) {
-        double h = dt;
-        if (h <= 0.0) {
-            if (t_end > 0.0 && tt >= t_end) break;
-            h = oracle_dt(c, q);
-            if (t_end > 0.0 && tt + h > t_end) h = t_end - tt;
+        /* Reading: with an end time, the step that would pass t_end is
+         * shortened to t_end - t and the time is then set to t_end exactly;
+         * no step is taken once t_end is reached (fixed or CFL steps). */
+        if (t_end > 0.0 && tt >= t_end) break;
+        double h = dt > 0.0 ? dt : oracle_dt(c, q);
+        int last = 0;
+        if (t_end > 0.0 && tt + h >= t_end) {
+            h = t_end - tt;
+            last = 1;
         }
         if (oracle_rk3_step(c, q, h)) return -1;
-        tt += h;
+        tt = last ? t_end : tt + h;
         ++taken;
     }
     if (t) *t = tt;

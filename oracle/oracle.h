@@ -118,8 +118,11 @@ double oracle_dt(const oracle_cfg* c, const double* q);
  * Pinned by: y' = lambda y gives 1 + z + z^2/2 + z^3/6. */
 int oracle_rk3_step(const oracle_cfg* c, double* q, double dt);
 
-/* nsteps SSP-RK3 steps with a fixed dt (dt > 0), or with CFL steps clipped to
- * end exactly at t_end (dt <= 0).  *t is advanced.  Returns steps taken. */
+/* Up to nsteps SSP-RK3 steps of fixed size dt (dt > 0) or CFL size (dt <= 0).
+ * With t_end > 0 the step that would pass t_end is shortened to land on it
+ * (time set to t_end exactly) and no step is taken once t_end is reached.
+ * *t (nullable) is the start time and receives the end time.  Returns the
+ * number of steps taken. */
 long oracle_run(const oracle_cfg* c, double* q, long nsteps, double dt,
                 double t_end, double* t);
 

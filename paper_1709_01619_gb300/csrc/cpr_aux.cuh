@@ -1,0 +1,313 @@
+// cpr_aux.cuh -- the passes around the stage kernel: element averages
+// (Algorithm 9), the troubled-cell limiter (Sec. 2.6 Eq. 35, Algorithms
+// 10-11), the initial max-speed pass of a CFL run (Eq. 36) and the FP64
+// norms.
+#pragma once
+
+#include "cpr_common.cuh"
+#include "cpr_reduce.cuh"
+
+namespace cpr {
+
+template <class T>
+struct AuxArgs {
+    T* q;             // state (limited in place by the limiter)
+    const T* ref;     // norms: reference state (nullable)
+    const T* avg_in;  // limiter: element averages of q
+    T* avg_out;       // averages kernel output
+    int* marks;       // limiter: marks[e]
+    T* wave;          // per-CTA partial max speed
+    Ctrl* ctrl;
+    double* partials; // norms: per-CTA FP64 partial results
+    long long ne, npts;
+    int nx, ny, bcx, bcy;
+    int do_wave;
+    int check_done;   // limiter inside a step: do nothing once t_end is reached
+    T hx, hy, tvb_M, lim_eps;
+    Phys<T> ph;
+    Tab<T> tab;
+    Tab<double> tab64;  // FP64 weights for the norms
+    double gamma64, ax64, ay64;
+};
+
+// Element average with the same operation order as the stage kernel: row sums
+// with the per-row weights, then the sum over rows.
+template <int N, int V, class T>
+__device__ __forceinline__ void element_average(const T* vals /* [V][N*N] */, const Tab<T>& tb, T* avg)
+{
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        T s = T(0);
+#pragma unroll
+        for (int b = 0; b < N; ++b) {
+            T r = tb.cavg[b][0] * vals[v * N * N + b * N];
+#pragma unroll
+            for (int a = 1; a < N; ++a) r = fma(tb.cavg[b][a], vals[v * N * N + b * N + a], r);
+            s = b == 0 ? r : s + r;
+        }
+        avg[v] = s;
+    }
+}
+
+// Elements per CTA of the element-wise passes: 64, or 32 where the staged
+// elements would not fit the 48 KB of static shared memory.
+template <class T, int P, int EQ>
+struct AuxShape {
+    static constexpr int N = P + 1, NN = N * N, V = NVars<EQ>::value;
+    static constexpr int EB = (V * kAuxElems * (NN + 1) * (int)sizeof(T) <= 48 * 1024) ? kAuxElems : kAuxElems / 2;
+};
+
+// Coalesced copy of EB consecutive elements into shared memory,
+// sm[(v * EB + le) * (NN + 1) + pt] (one pad word against bank conflicts
+// when each thread walks its own element).
+template <int N, int V, int EB, class T>
+__device__ __forceinline__ void load_elements(const T* __restrict__ q, long long npts, long long e0, int cnt,
+                                              T* sm)
+{
+    constexpr int NN = N * N;
+    for (int v = 0; v < V; ++v) {
+        const T* src = q + v * npts + e0 * NN;
+        for (int idx = threadIdx.x; idx < cnt * NN; idx += blockDim.x)
+            sm[(v * EB + idx / NN) * (NN + 1) + idx % NN] = src[idx];
+    }
+}
+
+template <class T, int P, int EQ>
+__global__ void __launch_bounds__(AuxShape<T, P, EQ>::EB) cpr_averages_kernel(const AuxArgs<T> A)
+{
+    constexpr int N = P + 1, NN = N * N, V = NVars<EQ>::value, EB = AuxShape<T, P, EQ>::EB;
+    __shared__ T sm[V * EB * (NN + 1)];
+    const long long e0 = (long long)blockIdx.x * EB;
+    const int cnt = (int)min((long long)EB, A.ne - e0);
+    load_elements<N, V, EB>(A.q, A.npts, e0, cnt, sm);
+    __syncthreads();
+    const int le = threadIdx.x;
+    if (le < cnt) {
+        T vals[V * NN], avg[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int pt = 0; pt < NN; ++pt) vals[v * NN + pt] = sm[(v * EB + le) * (NN + 1) + pt];
+        element_average<N, V>(vals, A.tab, avg);
+#pragma unroll
+        for (int v = 0; v < V; ++v) A.avg_out[v * A.ne + e0 + le] = avg[v];
+    }
+}
+
+// TVB-modified minmod: keep the first argument when |a| <= M h^2.
+template <class T>
+__device__ __forceinline__ T minmod_tvb(T a, T b, T c, T M, T h)
+{
+    const T aa = a >= T(0) ? a : -a;
+    if (aa <= M * h * h) return a;
+    return minmod3(a, b, c);
+}
+
+// Troubled-cell limiter.  One thread per element.
+// Marking (Algorithm 10): for every variable and every edge point, the
+// outward edge deviation delta = s (q_edge - qbar) (s = +1 on right/top edges,
+// -1 on left/bottom) is compared with the TVB minmod of delta and the
+// differences of the neighbouring averages across that edge; the element is
+// marked when |delta - mt| > eps anywhere (the OR over edge points of
+// Algorithm 11).  Limiting (Eq. 35, per direction): q_ab = qbar
+// + (xi_a hx / 2) mm(Dx+ / hx, Dx- / hx) + (eta_b hy / 2) mm(Dy+ / hy, Dy- / hy).
+// A transmissive boundary contributes a ghost average equal to the element's
+// own average.
+template <class T, int P, int EQ>
+__global__ void __launch_bounds__(AuxShape<T, P, EQ>::EB) cpr_limit_kernel(const AuxArgs<T> A)
+{
+    constexpr int N = P + 1, NN = N * N, V = NVars<EQ>::value, EB = AuxShape<T, P, EQ>::EB;
+    __shared__ T sm[V * EB * (NN + 1)];
+    if (A.check_done && A.ctrl->done) return;  // uniform exit
+    const long long e0 = (long long)blockIdx.x * EB;
+    const int cnt = (int)min((long long)EB, A.ne - e0);
+    load_elements<N, V, EB>(A.q, A.npts, e0, cnt, sm);
+    __syncthreads();
+    const int le = threadIdx.x;
+    const Tab<T>& tb = A.tab;
+    int marked = 0;
+    T m = T(0);
+    if (le < cnt) {
+        const long long e = e0 + le;
+        const int i = (int)(e % A.nx), j = (int)(e / A.nx);
+        long long eL = i > 0 ? e - 1 : (A.bcx ? -1 : e + A.nx - 1);
+        long long eR = i < A.nx - 1 ? e + 1 : (A.bcx ? -1 : e - (A.nx - 1));
+        long long eB = j > 0 ? e - A.nx : (A.bcy ? -1 : e + (long long)A.nx * (A.ny - 1));
+        long long eT = j < A.ny - 1 ? e + A.nx : (A.bcy ? -1 : e - (long long)A.nx * (A.ny - 1));
+        T vals[V * NN];
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int pt = 0; pt < NN; ++pt) vals[v * NN + pt] = sm[(v * EB + le) * (NN + 1) + pt];
+        T worst = -T(1e30);
+        T qk[V], aL[V], aR[V], aB[V], aT[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            qk[v] = A.avg_in[v * A.ne + e];
+            aL[v] = eL >= 0 ? A.avg_in[v * A.ne + eL] : qk[v];
+            aR[v] = eR >= 0 ? A.avg_in[v * A.ne + eR] : qk[v];
+            aB[v] = eB >= 0 ? A.avg_in[v * A.ne + eB] : qk[v];
+            aT[v] = eT >= 0 ? A.avg_in[v * A.ne + eT] : qk[v];
+            const T dxp = aR[v] - qk[v], dxm = qk[v] - aL[v];
+            const T dyp = aT[v] - qk[v], dym = qk[v] - aB[v];
+#pragma unroll
+            for (int kk = 0; kk < N; ++kk) {
+                T row[N], col[N];
+#pragma unroll
+                for (int l = 0; l < N; ++l) {
+                    row[l] = vals[v * NN + kk * N + l];
+                    col[l] = vals[v * NN + l * N + kk];
+                }
+                T sL = tb.lm[0] * row[0], sR = tb.lp[0] * row[0];
+                T sB = tb.lm[0] * col[0], sT = tb.lp[0] * col[0];
+#pragma unroll
+                for (int l = 1; l < N; ++l) {
+                    sL = fma(tb.lm[l], row[l], sL);
+                    sR = fma(tb.lp[l], row[l], sR);
+                    sB = fma(tb.lm[l], col[l], sB);
+                    sT = fma(tb.lp[l], col[l], sT);
+                }
+                T d, dev;
+                d = qk[v] - sL;
+                dev = d - minmod_tvb(d, dxp, dxm, A.tvb_M, A.hx);
+                dev = (dev >= T(0) ? dev : -dev) - A.lim_eps;
+                worst = dev > worst ? dev : worst;
+                d = sR - qk[v];
+                dev = d - minmod_tvb(d, dxp, dxm, A.tvb_M, A.hx);
+                dev = (dev >= T(0) ? dev : -dev) - A.lim_eps;
+                worst = dev > worst ? dev : worst;
+                d = qk[v] - sB;
+                dev = d - minmod_tvb(d, dyp, dym, A.tvb_M, A.hy);
+                dev = (dev >= T(0) ? dev : -dev) - A.lim_eps;
+                worst = dev > worst ? dev : worst;
+                d = sT - qk[v];
+                dev = d - minmod_tvb(d, dyp, dym, A.tvb_M, A.hy);
+                dev = (dev >= T(0) ? dev : -dev) - A.lim_eps;
+                worst = dev > worst ? dev : worst;
+            }
+        }
+        marked = worst > T(0);
+        A.marks[e] = marked;
+        if (marked) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const T sx = minmod2((aR[v] - qk[v]) / A.hx, (qk[v] - aL[v]) / A.hx);
+                const T sy = minmod2((aT[v] - qk[v]) / A.hy, (qk[v] - aB[v]) / A.hy);
+#pragma unroll
+                for (int b = 0; b < N; ++b)
+#pragma unroll
+                    for (int a = 0; a < N; ++a) {
+                        const T x = (T(0.5) * A.hx * tb.xi[a]) * sx;
+                        const T y = (T(0.5) * A.hy * tb.xi[b]) * sy;
+                        const T val = (qk[v] + x) + y;
+                        vals[v * NN + b * N + a] = val;
+                        A.q[v * A.npts + e * NN + b * N + a] = val;
+                    }
+            }
+        }
+        if (A.do_wave) {
+#pragma unroll
+            for (int pt = 0; pt < NN; ++pt) {
+                T qp[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) qp[v] = vals[v * NN + pt];
+                const T s = point_speed<EQ>(qp, A.ph);
+                m = s > m ? s : m;
+            }
+        }
+    }
+    // count of marked elements (integer: order-independent)
+    __shared__ int s_cnt;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    if (marked) atomicAdd(&s_cnt, 1);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_cnt) atomicAdd(reinterpret_cast<unsigned long long*>(&A.ctrl->marked),
+                                             (unsigned long long)s_cnt);
+    if (A.do_wave) {
+        m = block_max<T>(m);
+        last_cta_time_update<T>(m, A.wave, A.ctrl, /*advance=*/true);
+    }
+}
+
+// Max signal speed of a state and the first step size of a CFL run.
+template <class T, int P, int EQ>
+__global__ void __launch_bounds__(256) cpr_wave_kernel(const AuxArgs<T> A)
+{
+    constexpr int V = NVars<EQ>::value;
+    T m = T(0);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < A.npts;
+         k += (long long)gridDim.x * blockDim.x) {
+        T qp[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) qp[v] = A.q[v * A.npts + k];
+        const T s = point_speed<EQ>(qp, A.ph);
+        m = s > m ? s : m;
+    }
+    m = block_max<T>(m);
+    last_cta_time_update<T>(m, A.wave, A.ctrl, /*advance=*/false);
+}
+
+// FP64 norms, pass 1: each CTA reduces a contiguous element range in a fixed
+// order and writes 8 partial values:
+//   [0..3] sum of element averages per variable, [4] sum (q - ref)^2,
+//   [5] sum ref^2, [6] max speed, [7] count of non-physical points.
+// The element average uses the FP64 weights w_a w_b / 4 in point order.
+constexpr int kNormThreads = 256;
+constexpr int kNormVals = 8;
+
+template <class T, int P, int EQ>
+__global__ void __launch_bounds__(kNormThreads) cpr_norms_kernel(const AuxArgs<T> A)
+{
+    constexpr int N = P + 1, NN = N * N, V = NVars<EQ>::value;
+    const long long chunk = (A.ne + gridDim.x - 1) / gridDim.x;
+    const long long eb = (long long)blockIdx.x * chunk;
+    const long long ee = min(A.ne, eb + chunk);
+    double acc[kNormVals] = {0, 0, 0, 0, 0, 0, 0, 0};
+    Phys<double> ph64;
+    ph64.gamma = A.gamma64;
+    ph64.ax = A.ax64;
+    ph64.ay = A.ay64;
+    for (long long e = eb + threadIdx.x; e < ee; e += blockDim.x) {
+        for (int v = 0; v < V; ++v) {
+            double s = 0.0;
+            for (int b = 0; b < N; ++b)
+                for (int a = 0; a < N; ++a)
+                    s = __dadd_rn(s, __dmul_rn(__dmul_rn(__dmul_rn(A.tab64.w[a], A.tab64.w[b]), 0.25),
+                                               (double)A.q[v * A.npts + e * NN + b * N + a]));
+            acc[v] += s;
+        }
+        for (int pt = 0; pt < NN; ++pt) {
+            double qp[4] = {0, 0, 0, 0};
+            for (int v = 0; v < V; ++v) {
+                const double x = (double)A.q[v * A.npts + e * NN + pt];
+                qp[v] = x;
+                if (A.ref) {
+                    const double r = (double)A.ref[v * A.npts + e * NN + pt];
+                    acc[4] += (x - r) * (x - r);
+                    acc[5] += r * r;
+                }
+            }
+            if (point_ok<EQ>(qp, ph64)) {
+                const double s = point_speed<EQ>(qp, ph64);
+                acc[6] = s > acc[6] ? s : acc[6];
+            } else {
+                acc[7] += 1.0;
+            }
+        }
+    }
+    __shared__ double red[kNormThreads][kNormVals];
+    for (int k = 0; k < kNormVals; ++k) red[threadIdx.x][k] = acc[k];
+    __syncthreads();
+    for (int s = kNormThreads / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int k = 0; k < kNormVals; ++k) {
+                if (k == 6) red[threadIdx.x][k] = fmax(red[threadIdx.x][k], red[threadIdx.x + s][k]);
+                else red[threadIdx.x][k] += red[threadIdx.x + s][k];
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x < kNormVals) A.partials[(long long)blockIdx.x * kNormVals + threadIdx.x] = red[0][threadIdx.x];
+}
+
+}  // namespace cpr

@@ -1,0 +1,73 @@
+// cpr_launch.h -- host-side interface between the C ABI and the per-dtype,
+// per-order kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "cpr_common.cuh"
+
+namespace cpr {
+
+// FP64 operator tables built on the host (see cpr_tables.cpp).
+struct HostTab {
+    int n;
+    double xi[kMaxN], w[kMaxN];
+    double D[kMaxN][kMaxN];  // D[a][l] = l_l'(xi_a)
+    double lm[kMaxN], lp[kMaxN];
+    double dgl[kMaxN], dgr[kMaxN];
+};
+
+// Fill *t for order p and point family pts (0 Gauss-Legendre, 1
+// Gauss-Lobatto).  Returns 0 on success.
+int build_tables(int p, int pts, HostTab* t);
+
+// Everything a launch needs, independent of the state dtype.
+struct LaunchCfg {
+    int eqn, p, div, flux;  // flux: FLUX_RUSANOV or FLUX_UPWIND
+    int nx, ny, bcx, bcy;
+    long long ne, npts;
+    double hx, hy, gamma, ax, ay, tvb_M, lim_eps;
+    HostTab tab;
+    Ctrl* ctrl;
+    void* wave;        // per-CTA partial max speeds (state dtype)
+    int* marks;        // limiter marks
+    double* partials;  // norms partials
+};
+
+constexpr int kTileX = 8, kTileY = 8;
+
+inline int stage_ctas(const LaunchCfg& c)
+{
+    return ((c.nx + kTileX - 1) / kTileX) * ((c.ny + kTileY - 1) / kTileY);
+}
+// upper bound on the CTAs of the element-wise passes (at least kAuxElems / 2
+// elements per CTA)
+inline int aux_ctas(const LaunchCfg& c) { return (int)((c.ne + kAuxElems / 2 - 1) / (kAuxElems / 2)); }
+
+// Stage kernel for one (dtype, order): mode 0 writes R(qs) to out; modes 1..3
+// write the SSP-RK3 stage.  avg (nullable) receives the element averages of
+// out; do_wave closes the step on the device (stage 3).
+template <class T, int P>
+cudaError_t launch_stage_p(const LaunchCfg& c, int mode, const void* qs, const void* qn, void* out,
+                           void* avg, bool do_wave, cudaStream_t s);
+template <class T, int P>
+cudaError_t prepare_stage_p(const LaunchCfg& c);
+
+template <class T>
+cudaError_t launch_stage(const LaunchCfg& c, int mode, const void* qs, const void* qn, void* out, void* avg,
+                         bool do_wave, cudaStream_t s);
+template <class T>
+cudaError_t prepare_stage(const LaunchCfg& c);
+template <class T>
+cudaError_t launch_averages(const LaunchCfg& c, const void* q, void* avg, cudaStream_t s);
+// role 0: stand-alone pass; 1: after stage 1 or 2 of a step (does nothing
+// once t_end is reached); 2: after stage 3 (also closes the step: the last
+// CTA advances the simulated time and sets the next step size).
+template <class T>
+cudaError_t launch_limit(const LaunchCfg& c, void* q, const void* avg, int role, cudaStream_t s);
+template <class T>
+cudaError_t launch_wave(const LaunchCfg& c, const void* q, cudaStream_t s);
+template <class T>
+cudaError_t launch_norms(const LaunchCfg& c, const void* q, const void* ref, int nblocks, cudaStream_t s);
+
+}  // namespace cpr

@@ -1,0 +1,107 @@
+// cpr_stage_inst.cuh -- launcher of the stage kernel for one (dtype, order);
+// included by one translation unit per (dtype, order) so that they compile
+// in parallel.
+#pragma once
+
+#include "cpr_launch.h"
+#include "cpr_stage.cuh"
+
+namespace cpr {
+
+template <class T>
+inline Tab<T> to_tab(const HostTab& h)
+{
+    Tab<T> t;
+    for (int a = 0; a < kMaxN; ++a) {
+        for (int l = 0; l < kMaxN; ++l) {
+            const bool in = a < h.n && l < h.n;
+            t.D[a][l] = in ? T(h.D[a][l]) : T(0);
+            t.cavg[a][l] = in ? T(h.w[a] * h.w[l] * 0.25) : T(0);
+        }
+        const bool in = a < h.n;
+        t.lm[a] = in ? T(h.lm[a]) : T(0);
+        t.lp[a] = in ? T(h.lp[a]) : T(0);
+        t.dgl[a] = in ? T(h.dgl[a]) : T(0);
+        t.dgr[a] = in ? T(h.dgr[a]) : T(0);
+        t.w[a] = in ? T(h.w[a]) : T(0);
+        t.xi[a] = in ? T(h.xi[a]) : T(0);
+    }
+    return t;
+}
+
+template <class T, int P, int EQ, int DIV, int FLUX>
+static cudaError_t stage_one(const LaunchCfg& c, const StageArgs<T>& A, int ctas, cudaStream_t s, bool prep)
+{
+    constexpr int N = P + 1, V = NVars<EQ>::value;
+    constexpr int NT = kTileX * kTileY * N;
+    const size_t smem = sizeof(T) * StageLayout<N, V, kTileX, kTileY>::TOTAL;
+    auto kern = cpr_stage_kernel<T, P, EQ, DIV, FLUX, kTileX, kTileY>;
+    if (prep) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<ctas, NT, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <class T, int P>
+static cudaError_t stage_dispatch(const LaunchCfg& c, const StageArgs<T>& A, int ctas, cudaStream_t s, bool prep)
+{
+    if (c.eqn == EQ_ADV) {
+        if (c.flux == FLUX_UPWIND)
+            return c.div == DIV_LP ? stage_one<T, P, EQ_ADV, DIV_LP, FLUX_UPWIND>(c, A, ctas, s, prep)
+                                   : stage_one<T, P, EQ_ADV, DIV_CHAIN, FLUX_UPWIND>(c, A, ctas, s, prep);
+        return c.div == DIV_LP ? stage_one<T, P, EQ_ADV, DIV_LP, FLUX_RUSANOV>(c, A, ctas, s, prep)
+                               : stage_one<T, P, EQ_ADV, DIV_CHAIN, FLUX_RUSANOV>(c, A, ctas, s, prep);
+    }
+    return c.div == DIV_LP ? stage_one<T, P, EQ_EULER, DIV_LP, FLUX_RUSANOV>(c, A, ctas, s, prep)
+                           : stage_one<T, P, EQ_EULER, DIV_CHAIN, FLUX_RUSANOV>(c, A, ctas, s, prep);
+}
+
+template <class T>
+static StageArgs<T> make_stage_args(const LaunchCfg& c, int mode, const void* qs, const void* qn, void* out,
+                                    void* avg, bool do_wave)
+{
+    StageArgs<T> A;
+    A.qs = static_cast<const T*>(qs);
+    A.qn = static_cast<const T*>(qn);
+    A.out = static_cast<T*>(out);
+    A.avg = static_cast<T*>(avg);
+    A.wave = static_cast<T*>(c.wave);
+    A.ctrl = c.ctrl;
+    A.npts = c.npts;
+    A.nx = c.nx;
+    A.ny = c.ny;
+    A.bcx = c.bcx;
+    A.bcy = c.bcy;
+    A.tiles_x = (c.nx + kTileX - 1) / kTileX;
+    A.mode = mode;
+    A.do_avg = avg != nullptr;
+    A.do_wave = do_wave;
+    A.rhx2 = T(2.0 / c.hx);
+    A.rhy2 = T(2.0 / c.hy);
+    A.ph.gamma = T(c.gamma);
+    A.ph.ax = T(c.ax);
+    A.ph.ay = T(c.ay);
+    A.tab = to_tab<T>(c.tab);
+    return A;
+}
+
+template <class T, int P>
+cudaError_t launch_stage_p(const LaunchCfg& c, int mode, const void* qs, const void* qn, void* out, void* avg,
+                           bool do_wave, cudaStream_t s)
+{
+    StageArgs<T> A = make_stage_args<T>(c, mode, qs, qn, out, avg, do_wave);
+    return stage_dispatch<T, P>(c, A, stage_ctas(c), s, false);
+}
+
+template <class T, int P>
+cudaError_t prepare_stage_p(const LaunchCfg& c)
+{
+    StageArgs<T> A = make_stage_args<T>(c, 0, nullptr, nullptr, nullptr, nullptr, false);
+    return stage_dispatch<T, P>(c, A, 0, 0, true);
+}
+
+}  // namespace cpr
+
+#define CPR_INSTANTIATE_STAGE(T, P)                                                                     \
+    template cudaError_t cpr::launch_stage_p<T, P>(const LaunchCfg&, int, const void*, const void*, void*, \
+                                                   void*, bool, cudaStream_t);                         \
+    template cudaError_t cpr::prepare_stage_p<T, P>(const LaunchCfg&);
