@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cpr", "reference"], default="cpr")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["vortex128", "vortex1024"], default="vortex128",
+                    help="vortex1024: only the HBM-sized case (a short run for profiling)")
     return ap.parse_args()
 
 
@@ -219,6 +221,46 @@ def run_reference(args, world, rank):
 # ---------------------------------------------------------------------------
 # CUDA path
 # ---------------------------------------------------------------------------
+def hbm_case(make, peak, steps=HBM_STEPS):
+    """1024^2 p=3 FP32 vortex (268 MB per state array, above L2): the stage
+    kernels of `steps` RK3 steps timed back to back with CUDA events."""
+    import torch
+    from paper_1709_01619_gb300 import _native as nat
+    cfgH, ctxH, q0H = make(nat.F32, HBM_NX)
+    qH = q0H.clone()
+    ctxH.step(qH, 3, 1e-4)
+    torch.cuda.synchronize()
+    eh = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    eh[0].record()
+    ctxH.step(qH, steps, 1e-4)
+    eh[1].record()
+    torch.cuda.synchronize()
+    msH = eh[0].elapsed_time(eh[1])
+    dofH = HBM_NX * HBM_NX * (P + 1) ** 2
+    launchH = msH / (3 * steps)
+    achievedH = dofH * 16 * (8.0 / 3.0) / (launchH * 1e-3) / 1e9
+    ctxH.close()
+    return {"workload": "euler_vortex_1024x1024_p3_fp32", "bound": "hbm", "achieved": achievedH,
+            "peak": peak, "unit": "GB/s", "frac": achievedH / peak, "launch_ms": launchH,
+            "dof_stage_per_s": dofH * 3 * steps / (msH * 1e-3), "rk3_steps": steps}
+
+
+def run_hbm_only(args):
+    import torch
+    from paper_1709_01619_gb300 import _native as nat
+    from paper_1709_01619_gb300 import inputs
+    peak, _ = peaks()
+
+    def make(dtype, nx):
+        cfg = nat.Config(eqn=nat.EULER, nx=nx, ny=nx, p=P, x1=L, y1=L, cfl=CFL, dtype=dtype)
+        ctx = nat.Context(cfg)
+        x, y = ctx.point_coords()
+        q0 = torch.tensor(inputs.vortex(x, y, eps=EPS), dtype=cfg.torch_dtype, device="cuda")
+        return cfg, ctx, q0
+
+    print(json.dumps(hbm_case(make, peak, max(1, args.steps))), flush=True)
+
+
 def run_cpr(args, world, rank, local):
     import torch
     from paper_1709_01619_gb300 import _native as nat
@@ -306,22 +348,7 @@ def run_cpr(args, world, rank, local):
     value64 = dof * 3 * n64 / (ms64 * 1e-3)
     del ctx64
 
-    # ---- HBM-sized case: 1024^2 p=3 FP32, stage kernels timed back to back ----
-    cfgH, ctxH, q0H = make(nat.F32, HBM_NX)
-    qH = q0H.clone()
-    ctxH.step(qH, 3, 1e-4)
-    torch.cuda.synchronize()
-    eh = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-    eh[0].record()
-    ctxH.step(qH, HBM_STEPS, 1e-4)
-    eh[1].record()
-    torch.cuda.synchronize()
-    msH = eh[0].elapsed_time(eh[1])
-    dofH = HBM_NX * HBM_NX * (P + 1) ** 2
-    launchH = msH / (3 * HBM_STEPS)
-    achievedH = dofH * 16 * (8.0 / 3.0) / (launchH * 1e-3) / 1e9
-    del ctxH, qH, q0H
-
+    hbm = hbm_case(make, peak)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, s, secs, thr = oracle_sample(12.0)
@@ -343,10 +370,7 @@ def run_cpr(args, world, rank, local):
                      "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
                      "kernel": "cpr_stage_kernel<float,3,Euler,LP,Rusanov>",
                      "note": "state (4.2 MB) is L2-resident at this size"},
-        "roofline_hbm_case": {"workload": "euler_vortex_1024x1024_p3_fp32", "bound": "hbm",
-                              "achieved": achievedH, "peak": peak, "unit": "GB/s",
-                              "frac": achievedH / peak, "launch_ms": launchH,
-                              "dof_stage_per_s": dofH * 3 * HBM_STEPS / (msH * 1e-3)},
+        "roofline_hbm_case": hbm,
         "f64": {"value": value64, "unit": UNIT, "ms_per_solve": ms64, "rk3_steps": n64,
                 "bound": "alu"},
         "l2_rho_avg_error": {"f32": err32, "f64": err64},
@@ -366,6 +390,8 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "vortex1024":
+        run_hbm_only(args)
     else:
         run_cpr(args, world, rank, local)
     if world > 1:
