@@ -204,6 +204,34 @@ cpr_status cpr_residual_vjp(cpr_ctx* ctx, const void* q_dev, const void* rbar_de
 cpr_status cpr_step_vjp(cpr_ctx* ctx, const void* q_dev, const void* qbar_out_dev, void* qbar_in_dev,
                         double dt);
 
+/* Largest state, in bytes, that cpr_step_noalloc accepts (16 MiB). */
+#define CPR_NOALLOC_MAX_STATE_BYTES (16u << 20)
+
+/* cpr_step_noalloc -- nsteps SSP-RK3 steps of fixed size dt on q_dev, in
+ * place, with no context and no device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot let a library
+ * allocate device memory, such as a host framework whose own pool allocator
+ * owns the device memory (an allocation behind its back can fail or break
+ * its accounting) or a latency-critical loop where cudaMalloc/cudaFree, which
+ * may synchronise the device, are not allowed.
+ *   cfg     problem description as for cpr_init; the limiter is not run
+ *           (cfg->limiter != 0 returns CPR_EINVAL) and cfl is ignored.
+ *   q_dev   device state array (layout and alignment as above), the only
+ *           memory the caller provides; it holds the result.
+ *   dt      step size (> 0); stream: cudaStream_t or NULL.
+ * The two stage buffers and the control block live in one file-scope device
+ * array of 2 * CPR_NOALLOC_MAX_STATE_BYTES + 256 bytes that every GPU loading
+ * libcpr.so holds until the process exits.  A state larger than
+ * CPR_NOALLOC_MAX_STATE_BYTES returns CPR_EINVAL before any work.  The first
+ * call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) for that device; make that first call before any
+ * stream capture.  All calls share the array and it keeps the previous
+ * call's contents: each call rewrites the control block first, and calls
+ * that overlap on the GPU (different streams, or host threads without
+ * ordering between them) race on it.  Returns CPR_ECUDA if the symbol
+ * lookup or a launch fails.  Simulated time is not tracked. */
+cpr_status cpr_step_noalloc(const cpr_config* cfg, void* q_dev, int nsteps, double dt, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,6 +33,7 @@ EXPORTS = (
     "cpr_init", "cpr_destroy", "cpr_state_elems", "cpr_last_error", "cpr_point_coords",
     "cpr_residual", "cpr_step", "cpr_step_host", "cpr_limit", "cpr_get_marks", "cpr_averages",
     "cpr_norms", "cpr_set_time", "cpr_get_time", "cpr_residual_vjp", "cpr_step_vjp",
+    "cpr_step_noalloc",
 )
 
 
