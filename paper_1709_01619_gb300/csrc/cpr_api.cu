@@ -41,8 +41,10 @@ struct cpr_ctx {
     Ctrl* h_ctrl = nullptr;        // pinned
     int norm_blocks = 1;
     void* host_state = nullptr;    // device copy for cpr_step_host
+    void* lo = nullptr;            // low part of the state (FP32 increment form)
+    bool use_inc = false;          // FP32 without limiter: increment form of SSP-RK3
     const void* graph_q = nullptr;
-    cudaGraphExec_t g1 = nullptr, gK = nullptr;
+    cudaGraphExec_t g1 = nullptr, g2 = nullptr, gK = nullptr;
     std::string err;
 };
 
@@ -77,7 +79,17 @@ __global__ void ctrl_configure_kernel(Ctrl* c, double dt_fixed, double t_end, do
     c->cfl_h = cfl_h;
     c->done = 0;
     c->counter = 0;
+    c->parity = 0;
     if (dt_fixed > 0.0) cpr::ctrl_next_dt(c, c->max_wave);
+}
+
+// Increment form: after an odd number of completed steps the state sits in
+// the context's second buffer; copy it back to the caller's array.
+__global__ void parity_copy_kernel(const Ctrl* c, float* dst, const float* src, long long n)
+{
+    if (!c->parity) return;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src[i];
 }
 
 __global__ void ctrl_set_time_kernel(Ctrl* c, double t, long long steps)
@@ -91,6 +103,12 @@ __global__ void ctrl_set_time_kernel(Ctrl* c, double t, long long steps)
 // ---------------------------------------------------------------------------
 // dtype dispatch
 // ---------------------------------------------------------------------------
+static cudaError_t stage_inc(cpr_ctx* c, int mode, const void* qs, const void* qb, void* out, bool wave,
+                             cudaStream_t s)
+{
+    cpr::StagePtrs b{qs, qb, nullptr, out, c->lo, nullptr};
+    return cpr::launch_stage<float>(c->lc, mode, b, wave, s);
+}
 static cudaError_t stage(cpr_ctx* c, int mode, const void* qs, const void* qn, void* out, void* avg, bool wave,
                          cudaStream_t s)
 {
@@ -151,7 +169,9 @@ static const char* validate(const cpr_config* c)
 static void free_all(cpr_ctx* c)
 {
     if (c->g1) cudaGraphExecDestroy(c->g1);
+    if (c->g2) cudaGraphExecDestroy(c->g2);
     if (c->gK) cudaGraphExecDestroy(c->gK);
+    cudaFree(c->lo);
     cudaFree(c->q1);
     cudaFree(c->q2);
     cudaFree(c->avg);
@@ -225,6 +245,8 @@ extern "C" cpr_status cpr_init(const cpr_config* cfg, void* stream, cpr_ctx** ou
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc(&c->q1, sbytes);
     if (e == cudaSuccess) e = cudaMalloc(&c->q2, sbytes);
+    c->use_inc = cfg->dtype == CPR_F32 && !cfg->limiter;
+    if (e == cudaSuccess && c->use_inc) e = cudaMalloc(&c->lo, sbytes);
     if (e == cudaSuccess) e = cudaMalloc(&c->avg, (size_t)c->V * c->ne * c->esize);
     if (e == cudaSuccess) e = cudaMalloc(&c->wave, (size_t)ctas * c->esize);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->marks, (size_t)c->ne * sizeof(int));
@@ -320,13 +342,28 @@ static cudaError_t enqueue_step(cpr_ctx* c, void* q, cudaStream_t s)
     return cudaSuccess;
 }
 
+// Increment form (FP32, no limiter), one step with the state's high part in
+// x: B1 -> y, B2 -> z, new high part -> y (B1 is dead by then).  The next
+// step runs with x and y swapped, so two steps bring the state back to x.
+static cudaError_t enqueue_inc_step(cpr_ctx* c, void* x, void* y, cudaStream_t s)
+{
+    cudaError_t e;
+    if ((e = stage_inc(c, cpr::MODE_INC1, x, nullptr, y, false, s)) != cudaSuccess) return e;
+    if ((e = stage_inc(c, cpr::MODE_INC2, x, y, c->q2, false, s)) != cudaSuccess) return e;
+    return stage_inc(c, cpr::MODE_INC3, x, c->q2, y, true, s);
+}
+
+// steps: 1 (one step from q), or an even count of alternating steps.
 static cudaError_t capture(cpr_ctx* c, void* q, int steps, cudaGraphExec_t* exec)
 {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     cudaError_t ee = cudaSuccess;
-    for (int k = 0; k < steps && ee == cudaSuccess; ++k) ee = enqueue_step(c, q, c->cap);
+    for (int k = 0; k < steps && ee == cudaSuccess; ++k) {
+        if (c->use_inc) ee = (k % 2 == 0) ? enqueue_inc_step(c, q, c->q1, c->cap) : enqueue_inc_step(c, c->q1, q, c->cap);
+        else ee = enqueue_step(c, q, c->cap);
+    }
     e = cudaStreamEndCapture(c->cap, &g);
     if (ee != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -340,12 +377,14 @@ static cudaError_t capture(cpr_ctx* c, void* q, int steps, cudaGraphExec_t* exec
 
 static cudaError_t ensure_graphs(cpr_ctx* c, void* q)
 {
-    if (c->graph_q == q && c->g1 && c->gK) return cudaSuccess;
+    if (c->graph_q == q && c->g1 && c->g2 && c->gK) return cudaSuccess;
     if (c->g1) cudaGraphExecDestroy(c->g1);
+    if (c->g2) cudaGraphExecDestroy(c->g2);
     if (c->gK) cudaGraphExecDestroy(c->gK);
-    c->g1 = c->gK = nullptr;
+    c->g1 = c->g2 = c->gK = nullptr;
     c->graph_q = nullptr;
     cudaError_t e = capture(c, q, 1, &c->g1);
+    if (e == cudaSuccess) e = capture(c, q, 2, &c->g2);
     if (e == cudaSuccess) e = capture(c, q, kStepsPerGraph, &c->gK);
     if (e == cudaSuccess) c->graph_q = q;
     return e;
@@ -365,8 +404,18 @@ extern "C" cpr_status cpr_step(cpr_ctx* c, void* q, int nsteps, double dt_fixed,
     CPR_CUDA(c, cudaGetLastError());
     if (dt_fixed <= 0.0) CPR_CUDA(c, wave(c, q, c->stream));
     CPR_CUDA(c, ensure_graphs(c, q));
+    if (c->use_inc) CPR_CUDA(c, cudaMemsetAsync(c->lo, 0, (size_t)c->nstate * c->esize, c->stream));
     for (int k = 0; k < nsteps / kStepsPerGraph; ++k) CPR_CUDA(c, cudaGraphLaunch(c->gK, c->stream));
-    for (int k = 0; k < nsteps % kStepsPerGraph; ++k) CPR_CUDA(c, cudaGraphLaunch(c->g1, c->stream));
+    const int rest = nsteps % kStepsPerGraph;
+    if (c->use_inc) {
+        for (int k = 0; k < rest / 2; ++k) CPR_CUDA(c, cudaGraphLaunch(c->g2, c->stream));
+        if (rest % 2) CPR_CUDA(c, cudaGraphLaunch(c->g1, c->stream));
+        parity_copy_kernel<<<1024, 256, 0, c->stream>>>(c->ctrl, static_cast<float*>(q),
+                                                        static_cast<const float*>(c->q1), c->nstate);
+        CPR_CUDA(c, cudaGetLastError());
+    } else {
+        for (int k = 0; k < rest; ++k) CPR_CUDA(c, cudaGraphLaunch(c->g1, c->stream));
+    }
     return CPR_OK;
 }
 

@@ -82,16 +82,23 @@ static AuxArgs<T> make_aux(const LaunchCfg& c)
     } while (0)
 
 template <class T>
+cudaError_t launch_stage(const LaunchCfg& c, int mode, const StagePtrs& b, bool do_wave, cudaStream_t s)
+{
+    switch (c.p) {
+    case 1: return launch_stage_p<T, 1>(c, mode, b, do_wave, s);
+    case 2: return launch_stage_p<T, 2>(c, mode, b, do_wave, s);
+    case 3: return launch_stage_p<T, 3>(c, mode, b, do_wave, s);
+    case 4: return launch_stage_p<T, 4>(c, mode, b, do_wave, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class T>
 cudaError_t launch_stage(const LaunchCfg& c, int mode, const void* qs, const void* qn, void* out, void* avg,
                          bool do_wave, cudaStream_t s)
 {
-    switch (c.p) {
-    case 1: return launch_stage_p<T, 1>(c, mode, qs, qn, out, avg, do_wave, s);
-    case 2: return launch_stage_p<T, 2>(c, mode, qs, qn, out, avg, do_wave, s);
-    case 3: return launch_stage_p<T, 3>(c, mode, qs, qn, out, avg, do_wave, s);
-    case 4: return launch_stage_p<T, 4>(c, mode, qs, qn, out, avg, do_wave, s);
-    default: return cudaErrorInvalidValue;
-    }
+    StagePtrs b{qs, nullptr, qn, out, nullptr, avg};
+    return launch_stage<T>(c, mode, b, do_wave, s);
 }
 
 template <class T>
@@ -176,6 +183,7 @@ cudaError_t launch_norms(const LaunchCfg& c, const void* q, const void* ref, int
 #define CPR_INSTANTIATE_AUX(T)                                                                              \
     template cudaError_t cpr::launch_stage<T>(const LaunchCfg&, int, const void*, const void*, void*, void*, \
                                               bool, cudaStream_t);                                          \
+    template cudaError_t cpr::launch_stage<T>(const LaunchCfg&, int, const StagePtrs&, bool, cudaStream_t);  \
     template cudaError_t cpr::prepare_stage<T>(const LaunchCfg&);                                            \
     template cudaError_t cpr::launch_averages<T>(const LaunchCfg&, const void*, void*, cudaStream_t);        \
     template cudaError_t cpr::launch_limit<T>(const LaunchCfg&, void*, const void*, int, cudaStream_t);      \

@@ -16,6 +16,13 @@ enum { EQ_ADV = 0, EQ_EULER = 1 };
 enum { DIV_LP = 0, DIV_CHAIN = 1 };
 enum { FLUX_RUSANOV = 0, FLUX_UPWIND = 1 };
 
+// What a stage-kernel launch computes (see cpr_stage.cuh).
+enum {
+    MODE_RESIDUAL = 0,
+    MODE_SO1 = 1, MODE_SO2 = 2, MODE_SO3 = 3,        // Shu-Osher stages
+    MODE_INC1 = 4, MODE_INC2 = 5, MODE_INC3 = 6      // increment stages
+};
+
 template <int EQ>
 struct NVars;
 template <>
@@ -56,7 +63,7 @@ struct Ctrl {
     unsigned int counter;  // CTA completion ticket for the last-CTA reduction
     int done;          // 1: t reached t_end, stage kernels do no work
     int last;          // 1: the step in flight was shortened to land on t_end
-    int pad;
+    int parity;        // steps completed in the current cpr_step call, mod 2
 };
 
 // Physics in the arithmetic type T.
@@ -68,6 +75,14 @@ struct Phys {
 
 __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
+
+// Reciprocal and square root inside the FP32 flux differences: the
+// hardware approximations (at most 2 ulp), whose error enters only through
+// quantities that multiply small differences.  FP64 keeps IEEE operations.
+__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float fsqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : sqrtf(x); }
+__device__ __forceinline__ double fsqrt(double x) { return sqrt(x); }
 
 // Pressure, Eq. 5: p = (gamma - 1)(e - (rho u u + rho v v)/2) with u = rho u / rho.
 template <class T>
@@ -197,6 +212,100 @@ __device__ __forceinline__ bool point_ok(const T* q, const Phys<T>& ph)
         }
     }
     return ok;
+}
+
+// Reference state of an element for the delta form: the conserved values
+// and the derived velocity, pressure and total enthalpy e + p.
+template <class T>
+struct Ref {
+    T q[4];
+    T u, v, p, H;
+};
+
+template <int EQ, class T>
+__device__ __forceinline__ Ref<T> make_ref(const T* q, const Phys<T>& ph)
+{
+    Ref<T> r;
+    constexpr int V = NVars<EQ>::value;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r.q[k] = k < V ? q[k] : T(0);
+    if constexpr (EQ == EQ_EULER) {
+        r.p = pressure(q, ph.gamma, r.u, r.v);
+        r.H = q[3] + r.p;
+    } else {
+        r.u = r.v = r.p = r.H = T(0);
+    }
+    return r;
+}
+
+// Flux difference f_DIR(ref + d) - f_DIR(ref) written with differences only
+// (exact algebra; every term is O(d)):
+//   du = (dm - u0 drho) / rho1,  d(m u) = dm u0 + m1 du,
+//   dp = (gamma - 1)(de - (d(m u) + d(n v)) / 2),
+//   d((e + p) u) = (de + dp) u0 + (H0 + de + dp) du,  and likewise in y.
+// Also returns the signal speed |Vn| + c of the state ref + d (speed).
+template <int EQ, int DIR, class T>
+__device__ __forceinline__ void dflux_speed(const Ref<T>& r, const T* d, const Phys<T>& ph, T* out, T& speed)
+{
+    if constexpr (EQ == EQ_ADV) {
+        const T an = DIR == 0 ? ph.ax : ph.ay;
+        out[0] = an * d[0];
+        speed = an >= T(0) ? an : -an;
+    } else {
+        const T inv = frcp(r.q[0] + d[0]);
+        const T du = (d[1] - r.u * d[0]) * inv;
+        const T dv = (d[2] - r.v * d[0]) * inv;
+        const T m1 = r.q[1] + d[1], n1 = r.q[2] + d[2];
+        const T dmu = d[1] * r.u + m1 * du;
+        const T dnv = d[2] * r.v + n1 * dv;
+        const T dp = (ph.gamma - T(1)) * (d[3] - T(0.5) * (dmu + dnv));
+        const T dH = d[3] + dp;
+        const T dvn = DIR == 0 ? du : dv;
+        const T vn0 = DIR == 0 ? r.u : r.v;
+        if (DIR == 0) {
+            out[0] = d[1];
+            out[1] = dmu + dp;
+            out[2] = d[2] * r.u + n1 * du;
+        } else {
+            out[0] = d[2];
+            out[1] = d[1] * r.v + m1 * dv;
+            out[2] = dnv + dp;
+        }
+        out[3] = dH * vn0 + (r.H + dH) * dvn;
+        const T vn1 = vn0 + dvn;
+        speed = (vn1 >= T(0) ? vn1 : -vn1) + fsqrt(ph.gamma * (r.p + dp) * inv);
+    }
+}
+
+template <int EQ, int DIR, class T>
+__device__ __forceinline__ void dflux(const Ref<T>& r, const T* d, const Phys<T>& ph, T* out)
+{
+    T s;
+    dflux_speed<EQ, DIR>(r, d, ph, out, s);
+}
+
+// Common flux relative to the reference: G = F*(ref + dm, ref + dp) - f(ref),
+// Rusanov (lambda = larger one-sided speed) or upwind (advection).
+template <int EQ, int FLUX, int DIR, class T>
+__device__ __forceinline__ void common_flux_delta(const Ref<T>& r, const T* dm, const T* dp, const Phys<T>& ph,
+                                                  T* G)
+{
+    if constexpr (EQ == EQ_ADV) {
+        const T an = DIR == 0 ? ph.ax : ph.ay;
+        if constexpr (FLUX == FLUX_UPWIND) {
+            G[0] = an >= T(0) ? an * dm[0] : an * dp[0];
+        } else {
+            const T lam = an >= T(0) ? an : -an;
+            G[0] = T(0.5) * (an * dm[0] + an * dp[0]) - T(0.5) * lam * (dp[0] - dm[0]);
+        }
+    } else {
+        T Fm[4], Fp[4], sm, sp;
+        dflux_speed<EQ, DIR>(r, dm, ph, Fm, sm);
+        dflux_speed<EQ, DIR>(r, dp, ph, Fp, sp);
+        const T lam = sm >= sp ? sm : sp;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) G[k] = T(0.5) * (Fm[k] + Fp[k]) - T(0.5) * lam * (dp[k] - dm[k]);
+    }
 }
 
 // Minmod functions of the limiter (Sec. 2.6).

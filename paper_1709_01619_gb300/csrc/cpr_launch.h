@@ -44,15 +44,29 @@ inline int stage_ctas(const LaunchCfg& c)
 // elements per CTA)
 inline int aux_ctas(const LaunchCfg& c) { return (int)((c.ne + kAuxElems / 2 - 1) / (kAuxElems / 2)); }
 
-// Stage kernel for one (dtype, order): mode 0 writes R(qs) to out; modes 1..3
-// write the SSP-RK3 stage.  avg (nullable) receives the element averages of
-// out; do_wave closes the step on the device (stage 3).
+// Buffers of one stage launch (see the modes of cpr_stage.cuh): qs the stage
+// input (hi of q^n in the increment modes), qb the increment added to it
+// (modes 5, 6), qn q^n (modes 2, 3), out the result, lo the low part of q^n
+// (mode 6, in place), avg the fused element averages of out (nullable).
+struct StagePtrs {
+    const void* qs;
+    const void* qb;
+    const void* qn;
+    void* out;
+    void* lo;
+    void* avg;
+};
+
+// Stage kernel for one (dtype, order).  do_wave closes the step on the
+// device (stage 3).
 template <class T, int P>
-cudaError_t launch_stage_p(const LaunchCfg& c, int mode, const void* qs, const void* qn, void* out,
-                           void* avg, bool do_wave, cudaStream_t s);
+cudaError_t launch_stage_p(const LaunchCfg& c, int mode, const StagePtrs& b, bool do_wave, cudaStream_t s);
 template <class T, int P>
 cudaError_t prepare_stage_p(const LaunchCfg& c);
 
+template <class T>
+cudaError_t launch_stage(const LaunchCfg& c, int mode, const StagePtrs& b, bool do_wave, cudaStream_t s);
+// Shu-Osher / residual form: modes 0..3.
 template <class T>
 cudaError_t launch_stage(const LaunchCfg& c, int mode, const void* qs, const void* qn, void* out, void* avg,
                          bool do_wave, cudaStream_t s);

@@ -64,6 +64,7 @@ __device__ __forceinline__ void ctrl_advance(Ctrl* c, double max_speed)
 {
     c->t = c->last ? c->t_end : c->t + c->dt;
     c->steps += 1;
+    c->parity ^= 1;
     ctrl_next_dt(c, max_speed);
 }
 

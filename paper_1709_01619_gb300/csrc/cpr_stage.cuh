@@ -4,23 +4,40 @@
 // point of the tile, the CPR right-hand side of Sec. 2.2 (Eq. 16-17)
 //   R_ab = -(2/hx) [ sum_l D_al f_lb + (F*_L,b - f_L,b) g_L'(xi_a) + (F*_R,b - f_R,b) g_R'(xi_a) ]
 //          -(2/hy) [ sum_l D_bl g_al + (G*_B,a - g_B,a) g_L'(eta_b) + (G*_T,a - g_T,a) g_R'(eta_b) ]
-// and then the stage update of the three-stage SSP Runge-Kutta scheme of
-// Sec. 4, out = cA q^n + cB (q_s + dt R), in one pass over HBM.
+// and then one stage of the three-stage SSP Runge-Kutta scheme of Sec. 4, in
+// one pass over HBM.  Two forms of the stage update:
+//   Shu-Osher (modes 1-3): q1 = q + dt R(q); q2 = 3/4 q + 1/4 (q1 + dt R(q1));
+//     q' = 1/3 q + 2/3 (q2 + dt R(q2)) -- the stage states are stored.
+//   increments (modes 4-6, FP32): the same scheme written as
+//     B1 = dt R(q); B2 = (B1 + dt R(q + B1)) / 4; q' = q + 2/3 (B2 + dt R(q + B2)),
+//     with q' accumulated in two floats (hi + lo, error-free transformation),
+//     so that the O(1e-3) update of an O(1) state does not lose its low bits
+//     every stage.  hi' goes to a second buffer (neighbour CTAs still read hi).
 //
-// Thread roles (N = p+1 points per direction, NT = TX*TY*N threads):
-//   thread (el, k) is the x-line "row k of element el" and the y-line
-//   "column k of element el".  Its row stays in registers from load to store;
-//   its column is read from the shared-memory copy of the tile.
-// Phases (barriers between them):
-//   1 load q_s rows (registers + shared), halo elements (shared)
-//   2 x-lines: flux, d/dxi (LP: of the flux; CR: chain rule), edge states;
-//     y-lines: same along eta; halo lines: edge states only
+// Thread roles (N = p+1 points per direction, NT = TX*TY*N threads): thread
+// (el, k) is the x-line "row k of element el" and the y-line "column k of
+// element el".  Its row comes from HBM into registers; its column is read
+// from the shared-memory copy of the tile.
+//
+// Delta form (FP32): every flux is evaluated as an exact algebraic difference
+// f(q_ref + d) - f(q_ref) from the state q_ref at point (0, 0) of its element.
+// The divergence and the edge terms only need flux differences (the rows of
+// D sum to zero, the edge weights sum to one), so the rounding error of the
+// O(1) flux values drops out.  The common flux on a face is formed relative
+// to the lower (left/bottom) element's reference; the upper element shifts it
+// by f(ref_upper) - f(ref_lower), one value per face.  FP64 evaluates the
+// fluxes directly (reference zero).
+//
+// Phases (one barrier after each):
+//   1 rows of the stage state into registers and shared memory, element
+//     references; halo lines (the edge states of the neighbour elements
+//     facing the tile) straight from L2
+//   2 x-lines and y-lines: flux differences, d/dxi and d/deta, edge states;
+//     reference shift of every face
 //   3 common flux on every face point of the tile (one evaluation per face)
-//   4 y-lines: correction along eta, y-part of R into shared memory
-//   5 x-lines: correction along xi, add y-part, stage update, store row;
-//     optional fused element averages (Algorithm 9) and max signal speed.
-// Element coupling (the only non-local data, Fig. 2) comes through the halo
-// ring of neighbour elements, which neighbouring CTAs read from L2.
+//   4 y-lines: y-part of R (shared accumulator)
+//   5 x-lines: x-part of R, stage update, store; optional fused element
+//     averages (Algorithm 9) and max signal speed of the result.
 #pragma once
 
 #include "cpr_common.cuh"
@@ -30,9 +47,11 @@ namespace cpr {
 
 template <class T>
 struct StageArgs {
-    const T* qs;      // stage input state
-    const T* qn;      // q^n (read when mode >= 2)
-    T* out;           // stage output (mode >= 1) or residual (mode 0)
+    const T* qs;      // stage input state (increment modes: hi of q^n)
+    const T* qb;      // increment modes 5, 6: B1 / B2, added to qs on load
+    const T* qn;      // Shu-Osher modes 2, 3: q^n
+    T* out;           // residual, stage state, increment, or hi of q^{n+1}
+    T* lo;            // mode 6: low part of q^n, updated in place
     T* avg;           // element averages of out (do_avg)
     T* wave;          // per-CTA partial max speed (do_wave)
     Ctrl* ctrl;       // time control (mode >= 1)
@@ -40,7 +59,7 @@ struct StageArgs {
     int nx, ny;
     int bcx, bcy;     // 1: transmissive
     int tiles_x;
-    int mode;         // 0: residual, 1..3: SSP-RK3 stage
+    int mode;
     int do_avg, do_wave;
     T rhx2, rhy2;     // 2/hx, 2/hy
     Phys<T> ph;
@@ -50,19 +69,30 @@ struct StageArgs {
 template <int N, int V, int TX, int TY>
 struct StageLayout {
     static constexpr int NN = N * N;
-    static constexpr int SQ = V * (TY + 2) * (TX + 2) * NN;  // tile + halo ring
-    static constexpr int XS = V * TY * (TX + 1) * N;         // one x-face array
-    static constexpr int YS = V * (TY + 1) * TX * N;         // one y-face array
-    static constexpr int TOTAL = SQ + 3 * XS + 3 * YS;
-    __device__ static int sq(int v, int ly, int lx, int pt) {
-        return ((v * (TY + 2) + ly) * (TX + 2) + lx) * NN + pt;
-    }
+    // element stride in the tile arrays: a multiple of 4 (16-byte rows) that
+    // spreads the column reads of neighbouring elements over the banks
+    static constexpr int ES = (NN % 4 == 0) ? NN + 4 : ((NN + 3) / 4) * 4;
+    static constexpr int E = TX * TY;
+    static constexpr int PE = (TX + 2) * (TY + 2);     // tile with its halo ring
+    static constexpr int NR = 8;                       // reference: q[4], u, v, p, H
+    static constexpr int SQ = V * E * ES;              // tile copy of the stage state
+    static constexpr int RS = V * E * ES;              // residual accumulator
+    static constexpr int XS = V * TY * (TX + 1) * N;   // one x-face array
+    static constexpr int YS = V * (TY + 1) * TX * N;   // one y-face array
+    static constexpr int RF = NR * PE;                 // element references
+    static constexpr int SH = V * (TY * (TX + 1) + (TY + 1) * TX);  // face shifts
+    static constexpr int TOTAL = SQ + RS + 3 * XS + 3 * YS + RF + SH;
+    __device__ static int sq(int v, int el, int pt) { return (v * E + el) * ES + pt; }
     __device__ static int xs(int v, int ty, int f, int k) { return ((v * TY + ty) * (TX + 1) + f) * N + k; }
     __device__ static int ys(int v, int g, int tx, int k) { return ((v * (TY + 1) + g) * TX + tx) * N + k; }
+    // reference of the element at tile coordinates (lx, ly), -1 <= lx <= TX
+    __device__ static int rf(int c, int lx, int ly) { return c * PE + (ly + 1) * (TX + 2) + (lx + 1); }
+    __device__ static int shx(int v, int ty, int f) { return (v * TY + ty) * (TX + 1) + f; }
+    __device__ static int shy(int v, int g, int tx) { return V * TY * (TX + 1) + (v * (TY + 1) + g) * TX + tx; }
 };
 
 // Edge value of a line of N values: sum_l c_l x_l, in one fixed fma order so
-// that every CTA computing the same trace gets the same bits.
+// that every CTA computing the same edge state gets the same bits.
 template <int N, class T>
 __device__ __forceinline__ T line_dot(const T* c, const T* x)
 {
@@ -72,53 +102,104 @@ __device__ __forceinline__ T line_dot(const T* c, const T* x)
     return s;
 }
 
-template <int N, int V, class T>
-__device__ __forceinline__ void load_row(const T* __restrict__ src, long long npts, T (&q)[N][V])
+template <int N, class T>
+__device__ __forceinline__ void gload_row(const T* __restrict__ s, T* x)
 {
+    if constexpr (sizeof(T) == 4 && N == 4) {
+        float4 t = *reinterpret_cast<const float4*>(s);
+        x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
+    } else if constexpr (sizeof(T) == 4 && N == 2) {
+        float2 t = *reinterpret_cast<const float2*>(s);
+        x[0] = t.x; x[1] = t.y;
+    } else if constexpr (sizeof(T) == 8 && N % 2 == 0) {
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-        const T* s = src + v * npts;
-        if constexpr (sizeof(T) == 4 && N == 4) {
-            float4 t = *reinterpret_cast<const float4*>(s);
-            q[0][v] = t.x; q[1][v] = t.y; q[2][v] = t.z; q[3][v] = t.w;
-        } else if constexpr (sizeof(T) == 4 && N == 2) {
-            float2 t = *reinterpret_cast<const float2*>(s);
-            q[0][v] = t.x; q[1][v] = t.y;
-        } else if constexpr (sizeof(T) == 8 && N % 2 == 0) {
-#pragma unroll
-            for (int a = 0; a < N; a += 2) {
-                double2 t = *reinterpret_cast<const double2*>(s + a);
-                q[a][v] = t.x; q[a + 1][v] = t.y;
-            }
-        } else {
-#pragma unroll
-            for (int a = 0; a < N; ++a) q[a][v] = s[a];
+        for (int a = 0; a < N; a += 2) {
+            double2 t = *reinterpret_cast<const double2*>(s + a);
+            x[a] = t.x; x[a + 1] = t.y;
         }
+    } else {
+#pragma unroll
+        for (int a = 0; a < N; ++a) x[a] = s[a];
     }
 }
 
-template <int N, int V, class T>
-__device__ __forceinline__ void store_row(T* __restrict__ dst, long long npts, const T (&o)[N][V])
+template <int N, class T>
+__device__ __forceinline__ void gstore_row(T* __restrict__ d, const T* x)
 {
+    if constexpr (sizeof(T) == 4 && N == 4) {
+        *reinterpret_cast<float4*>(d) = make_float4(x[0], x[1], x[2], x[3]);
+    } else if constexpr (sizeof(T) == 4 && N == 2) {
+        *reinterpret_cast<float2*>(d) = make_float2(x[0], x[1]);
+    } else if constexpr (sizeof(T) == 8 && N % 2 == 0) {
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-        T* d = dst + v * npts;
-        if constexpr (sizeof(T) == 4 && N == 4) {
-            *reinterpret_cast<float4*>(d) = make_float4(o[0][v], o[1][v], o[2][v], o[3][v]);
-        } else if constexpr (sizeof(T) == 4 && N == 2) {
-            *reinterpret_cast<float2*>(d) = make_float2(o[0][v], o[1][v]);
-        } else if constexpr (sizeof(T) == 8 && N % 2 == 0) {
+        for (int a = 0; a < N; a += 2) *reinterpret_cast<double2*>(d + a) = make_double2(x[a], x[a + 1]);
+    } else {
 #pragma unroll
-            for (int a = 0; a < N; a += 2) *reinterpret_cast<double2*>(d + a) = make_double2(o[a][v], o[a + 1][v]);
-        } else {
-#pragma unroll
-            for (int a = 0; a < N; ++a) d[a] = o[a][v];
-        }
+        for (int a = 0; a < N; ++a) d[a] = x[a];
     }
 }
 
-template <class T, int P, int EQ, int DIV, int FLUX, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY * (P + 1))
+// Row of N values of one variable in shared memory (16-byte aligned when N = 4).
+template <int N, class T>
+__device__ __forceinline__ void sm_store_row(T* d, const T* x)
+{
+    if constexpr (sizeof(T) == 4 && N == 4) {
+        *reinterpret_cast<float4*>(d) = make_float4(x[0], x[1], x[2], x[3]);
+    } else {
+#pragma unroll
+        for (int a = 0; a < N; ++a) d[a] = x[a];
+    }
+}
+
+template <int N, class T>
+__device__ __forceinline__ void sm_load_row(const T* s, T* x)
+{
+    if constexpr (sizeof(T) == 4 && N == 4) {
+        float4 t = *reinterpret_cast<const float4*>(s);
+        x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
+    } else {
+#pragma unroll
+        for (int a = 0; a < N; ++a) x[a] = s[a];
+    }
+}
+
+// Flux difference f_DIR(ref + d) - f_DIR(ref) (delta form) or f_DIR(d) (plain).
+template <int EQ, int DIR, bool DELTA, class T>
+__device__ __forceinline__ void line_flux(const Ref<T>& r, const T* d, const Phys<T>& ph, T* out)
+{
+    if constexpr (DELTA) dflux<EQ, DIR>(r, d, ph, out);
+    else if constexpr (DIR == 0) flux_x<EQ>(d, ph, out);
+    else flux_y<EQ>(d, ph, out);
+}
+
+// q' = hi + lo + D as hi' + lo' (Knuth's two-sum of hi and D, then the old
+// and new low parts folded back); the pair keeps about 48 bits.
+__device__ __forceinline__ void compensated_add(float& hi, float& lo, float D)
+{
+    const float s = __fadd_rn(hi, D);
+    const float bv = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(D, bv));
+    const float e = __fadd_rn(err, lo);
+    const float h2 = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(h2, s));
+    hi = h2;
+}
+__device__ __forceinline__ void compensated_add(double& hi, double& lo, double D)
+{
+    hi += D + lo;
+    lo = 0.0;
+}
+
+// Resident CTAs per SM the register budget is sized for (FP32: as many as the
+// shared memory allows; FP64: one).
+template <class T, int N>
+constexpr int stage_min_blocks()
+{
+    return sizeof(T) == 8 ? 1 : (N <= 3 ? 3 : 2);
+}
+
+template <class T, int P, int EQ, int DIV, int FLUX, int TX, int TY, bool DELTA>
+__global__ void __launch_bounds__(TX * TY * (P + 1), (stage_min_blocks<T, P + 1>()))
 cpr_stage_kernel(const StageArgs<T> A)
 {
     constexpr int N = P + 1, NN = N * N, V = NVars<EQ>::value;
@@ -126,14 +207,16 @@ cpr_stage_kernel(const StageArgs<T> A)
     using L = StageLayout<N, V, TX, TY>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sq = reinterpret_cast<T*>(smem_raw);
-    T* xL = sq + L::SQ;  // left edge state of elements 0..TXe (index = element)
+    T* rS = sq + L::SQ;  // residual accumulator, same layout as sq
+    T* xL = rS + L::RS;  // left edge state (delta) of elements 0..TXe (index = element)
     T* xR = xL + L::XS;  // right edge state of elements -1..TXe-1 (index = element + 1)
-    T* xF = xR + L::XS;  // common flux on x-faces 0..TXe (face f between elements f-1, f)
+    T* xF = xR + L::XS;  // common flux minus f(lower reference) on x-faces 0..TXe
     T* yB = xF + L::XS;
     T* yT = yB + L::YS;
     T* yG = yT + L::YS;
-    T* ryS = sq;         // y-part of R, reuses the tile copy once it is dead
-    T* avS = xL;         // row partial sums of the averages, reuses xL
+    T* rfS = yG + L::YS; // element references over the tile and its halo ring
+    T* shS = rfS + L::RF;
+    T* avS = xL;         // row partial sums of the averages, reuses xL after phase 3
 
     if (A.mode > 0 && A.ctrl->done) return;  // t_end reached: uniform exit
 
@@ -146,57 +229,148 @@ cpr_stage_kernel(const StageArgs<T> A)
     const bool valid = tx < TXe && ty < TYe;
     const long long e = (long long)(j0 + ty) * A.nx + (i0 + tx);
     const Tab<T>& tb = A.tab;
+    const bool addb = A.mode == MODE_INC2 || A.mode == MODE_INC3;
 
-    // ---- phase 1: load ----------------------------------------------------
-    T q[N][V];
+    // ---- phase 1: tile rows, references, halo lines -----------------------
     if (valid) {
-        load_row<N, V>(A.qs + e * NN + k * N, A.npts, q);
 #pragma unroll
-        for (int v = 0; v < V; ++v)
+        for (int v = 0; v < V; ++v) {
+            T row[N];
+            gload_row<N>(A.qs + v * A.npts + e * NN + k * N, row);
+            if (addb) {
+                T b[N];
+                gload_row<N>(A.qb + v * A.npts + e * NN + k * N, b);
 #pragma unroll
-            for (int a = 0; a < N; ++a) sq[L::sq(v, ty + 1, tx + 1, k * N + a)] = q[a][v];
+                for (int a = 0; a < N; ++a) row[a] += b[a];
+            }
+            sm_store_row<N>(sq + L::sq(v, el, k * N), row);
+            if (DELTA && k == 0) rfS[L::rf(v, tx, ty)] = row[0];
+        }
     }
     {
-        const int nh = 2 * TYe + 2 * TXe;
-        for (int idx = tid; idx < nh * NN; idx += NT) {
-            const int h = idx / NN, pt = idx % NN;
-            int lx, ly;
-            if (h < TYe) { lx = -1; ly = h; }
-            else if (h < 2 * TYe) { lx = TXe; ly = h - TYe; }
-            else if (h < 2 * TYe + TXe) { lx = h - 2 * TYe; ly = -1; }
-            else { lx = h - 2 * TYe - TXe; ly = TYe; }
-            int gi = i0 + lx, gj = j0 + ly;
-            if (gi < 0 || gi >= A.nx) {
-                if (A.bcx) continue;
-                gi = (gi + A.nx) % A.nx;
-            }
-            if (gj < 0 || gj >= A.ny) {
-                if (A.bcy) continue;
-                gj = (gj + A.ny) % A.ny;
+        constexpr int NXH = 2 * TY * N, NYH = 2 * TX * N;
+        for (int t = tid; t < NXH + NYH; t += NT) {
+            const bool xdir = t < NXH;
+            const int r0 = xdir ? t : t - NXH;
+            const int side = xdir ? r0 / (TY * N) : r0 / (TX * N);
+            const int r = xdir ? r0 % (TY * N) : r0 % (TX * N);
+            const int pos = r / N, kk = r % N;  // pos: tile row (x) or tile column (y)
+            if (pos >= (xdir ? TYe : TXe)) continue;
+            int gi, gj;
+            if (xdir) {
+                gi = side ? i0 + TXe : i0 - 1;
+                gj = j0 + pos;
+                if (gi < 0 || gi >= A.nx) {
+                    if (A.bcx) continue;
+                    gi = gi < 0 ? gi + A.nx : gi - A.nx;
+                }
+            } else {
+                gi = i0 + pos;
+                gj = side ? j0 + TYe : j0 - 1;
+                if (gj < 0 || gj >= A.ny) {
+                    if (A.bcy) continue;
+                    gj = gj < 0 ? gj + A.ny : gj - A.ny;
+                }
             }
             const long long eh = (long long)gj * A.nx + gi;
+            const int lx = xdir ? (side ? TXe : -1) : pos;
+            const int ly = xdir ? pos : (side ? TYe : -1);
+            const T* coef = side ? tb.lm : tb.lp;  // the edge facing the tile
 #pragma unroll
-            for (int v = 0; v < V; ++v) sq[L::sq(v, ly + 1, lx + 1, pt)] = A.qs[v * A.npts + eh * NN + pt];
+            for (int v = 0; v < V; ++v) {
+                const T* src = A.qs + v * A.npts + eh * NN;
+                const T* srb = addb ? A.qb + v * A.npts + eh * NN : src;
+                T ref = T(0);
+                if (DELTA) ref = addb ? src[0] + srb[0] : src[0];
+                T line[N];
+                if (xdir) {
+                    gload_row<N>(src + kk * N, line);
+                    if (addb) {
+                        T b[N];
+                        gload_row<N>(srb + kk * N, b);
+#pragma unroll
+                        for (int l = 0; l < N; ++l) line[l] += b[l];
+                    }
+                } else {
+#pragma unroll
+                    for (int l = 0; l < N; ++l) line[l] = addb ? src[l * N + kk] + srb[l * N + kk] : src[l * N + kk];
+                }
+#pragma unroll
+                for (int l = 0; l < N; ++l) line[l] -= ref;
+                const T d = line_dot<N>(coef, line);
+                if (xdir) {
+                    if (side) xL[L::xs(v, pos, TXe, kk)] = d;
+                    else xR[L::xs(v, pos, 0, kk)] = d;
+                } else {
+                    if (side) yB[L::ys(v, TYe, pos, kk)] = d;
+                    else yT[L::ys(v, 0, pos, kk)] = d;
+                }
+                if (DELTA && kk == 0) rfS[L::rf(v, lx, ly)] = ref;
+            }
+        }
+    }
+    __syncthreads();
+    // derived reference quantities (u, v, p, H) of every element in reach
+    if constexpr (DELTA && EQ == EQ_EULER) {
+        for (int c = tid; c < L::PE; c += NT) {
+            const int lx = c % (TX + 2) - 1, ly = c / (TX + 2) - 1;
+            const bool tile = lx >= 0 && lx < TXe && ly >= 0 && ly < TYe;
+            const bool xh = (lx == -1 || lx == TXe) && ly >= 0 && ly < TYe;
+            const bool yh = (ly == -1 || ly == TYe) && lx >= 0 && lx < TXe;
+            if (!(tile || xh || yh)) continue;
+            const int gi = i0 + lx, gj = j0 + ly;
+            if ((A.bcx && (gi < 0 || gi >= A.nx)) || (A.bcy && (gj < 0 || gj >= A.ny))) continue;
+            T q0[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) q0[v] = rfS[L::rf(v, lx, ly)];
+            const Ref<T> r = make_ref<EQ>(q0, A.ph);
+            rfS[L::rf(4, lx, ly)] = r.u;
+            rfS[L::rf(5, lx, ly)] = r.v;
+            rfS[L::rf(6, lx, ly)] = r.p;
+            rfS[L::rf(7, lx, ly)] = r.H;
         }
     }
     __syncthreads();
 
-    // ---- phase 2: line operators ----------------------------------------
+    auto load_ref = [&](int lx, int ly) {
+        Ref<T> r;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) r.q[v] = v < V ? rfS[L::rf(v, lx, ly)] : T(0);
+        if constexpr (EQ == EQ_EULER) {
+            r.u = rfS[L::rf(4, lx, ly)];
+            r.v = rfS[L::rf(5, lx, ly)];
+            r.p = rfS[L::rf(6, lx, ly)];
+            r.H = rfS[L::rf(7, lx, ly)];
+        } else {
+            r.u = r.v = r.p = r.H = T(0);
+        }
+        return r;
+    };
+
+    // ---- phase 2: line operators, face shifts --------------------------------
+    Ref<T> rf;
     T rx[N][V], ry[N][V];
     T fL[V], fR[V], gB[V], gT[V];
     if (valid) {
-        // x-line: row k of element el, held in registers
-        T f[N][V];
+        if constexpr (DELTA) rf = load_ref(tx, ty);
+        // x-line: row k
+        T d[N][V], f[N][V], col[N];
 #pragma unroll
-        for (int a = 0; a < N; ++a) flux_x<EQ>(q[a], A.ph, f[a]);
-        T col[N];
-        T qL[V], qR[V];
+        for (int v = 0; v < V; ++v) {
+            T row[N];
+            sm_load_row<N>(sq + L::sq(v, el, k * N), row);
+#pragma unroll
+            for (int a = 0; a < N; ++a) d[a][v] = DELTA ? row[a] - rf.q[v] : row[a];
+        }
+#pragma unroll
+        for (int a = 0; a < N; ++a) line_flux<EQ, 0, DELTA>(rf, d[a], A.ph, f[a]);
+        T eL[V], eR[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
 #pragma unroll
-            for (int l = 0; l < N; ++l) col[l] = q[l][v];
-            qL[v] = line_dot<N>(tb.lm, col);
-            qR[v] = line_dot<N>(tb.lp, col);
+            for (int l = 0; l < N; ++l) col[l] = d[l][v];
+            eL[v] = line_dot<N>(tb.lm, col);
+            eR[v] = line_dot<N>(tb.lp, col);
         }
         if constexpr (DIV == DIV_LP) {
 #pragma unroll
@@ -211,44 +385,47 @@ cpr_stage_kernel(const StageArgs<T> A)
         } else {
 #pragma unroll
             for (int a = 0; a < N; ++a) {
-                T dq[V];
+                T dq[V], qa[V];
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
 #pragma unroll
-                    for (int l = 0; l < N; ++l) col[l] = q[l][v];
+                    for (int l = 0; l < N; ++l) col[l] = d[l][v];
                     dq[v] = line_dot<N>(tb.D[a], col);
+                    qa[v] = DELTA ? rf.q[v] + d[a][v] : d[a][v];
                 }
-                flux_jvp<EQ, 0>(q[a], dq, A.ph, rx[a]);
+                flux_jvp<EQ, 0>(qa, dq, A.ph, rx[a]);
             }
-            flux_x<EQ>(qL, A.ph, fL);
-            flux_x<EQ>(qR, A.ph, fR);
+            line_flux<EQ, 0, DELTA>(rf, eL, A.ph, fL);
+            line_flux<EQ, 0, DELTA>(rf, eR, A.ph, fR);
         }
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            xL[L::xs(v, ty, tx, k)] = qL[v];
-            xR[L::xs(v, ty, tx + 1, k)] = qR[v];
+            xL[L::xs(v, ty, tx, k)] = eL[v];
+            xR[L::xs(v, ty, tx + 1, k)] = eR[v];
         }
-        // y-line: column k of element el, from shared memory
-        T c[N][V], g[N][V];
+        // y-line: column k
 #pragma unroll
         for (int b = 0; b < N; ++b)
 #pragma unroll
-            for (int v = 0; v < V; ++v) c[b][v] = sq[L::sq(v, ty + 1, tx + 1, b * N + k)];
+            for (int v = 0; v < V; ++v) {
+                const T x = sq[L::sq(v, el, b * N + k)];
+                d[b][v] = DELTA ? x - rf.q[v] : x;
+            }
 #pragma unroll
-        for (int b = 0; b < N; ++b) flux_y<EQ>(c[b], A.ph, g[b]);
-        T qB[V], qT[V];
+        for (int b = 0; b < N; ++b) line_flux<EQ, 1, DELTA>(rf, d[b], A.ph, f[b]);
+        T eB[V], eT[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
 #pragma unroll
-            for (int l = 0; l < N; ++l) col[l] = c[l][v];
-            qB[v] = line_dot<N>(tb.lm, col);
-            qT[v] = line_dot<N>(tb.lp, col);
+            for (int l = 0; l < N; ++l) col[l] = d[l][v];
+            eB[v] = line_dot<N>(tb.lm, col);
+            eT[v] = line_dot<N>(tb.lp, col);
         }
         if constexpr (DIV == DIV_LP) {
 #pragma unroll
             for (int v = 0; v < V; ++v) {
 #pragma unroll
-                for (int l = 0; l < N; ++l) col[l] = g[l][v];
+                for (int l = 0; l < N; ++l) col[l] = f[l][v];
 #pragma unroll
                 for (int b = 0; b < N; ++b) ry[b][v] = line_dot<N>(tb.D[b], col);
                 gB[v] = line_dot<N>(tb.lm, col);
@@ -257,151 +434,187 @@ cpr_stage_kernel(const StageArgs<T> A)
         } else {
 #pragma unroll
             for (int b = 0; b < N; ++b) {
-                T dq[V];
+                T dq[V], qb[V];
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
 #pragma unroll
-                    for (int l = 0; l < N; ++l) col[l] = c[l][v];
+                    for (int l = 0; l < N; ++l) col[l] = d[l][v];
                     dq[v] = line_dot<N>(tb.D[b], col);
+                    qb[v] = DELTA ? rf.q[v] + d[b][v] : d[b][v];
                 }
-                flux_jvp<EQ, 1>(c[b], dq, A.ph, ry[b]);
+                flux_jvp<EQ, 1>(qb, dq, A.ph, ry[b]);
             }
-            flux_y<EQ>(qB, A.ph, gB);
-            flux_y<EQ>(qT, A.ph, gT);
+            line_flux<EQ, 1, DELTA>(rf, eB, A.ph, gB);
+            line_flux<EQ, 1, DELTA>(rf, eT, A.ph, gT);
         }
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            yB[L::ys(v, ty, tx, k)] = qB[v];
-            yT[L::ys(v, ty + 1, tx, k)] = qT[v];
+            yB[L::ys(v, ty, tx, k)] = eB[v];
+            yT[L::ys(v, ty + 1, tx, k)] = eT[v];
         }
     }
-    {
-        // edge states of the halo elements facing the tile
-        const int nxh = 2 * TYe * N, nyh = 2 * TXe * N;
-        for (int task = tid; task < nxh + nyh; task += NT) {
-            T col[N];
-            if (task < nxh) {
-                const int side = task / (TYe * N), r = task % (TYe * N);
-                const int ly = r / N, kk = r % N;
-                const int lx = side ? TXe : -1;
-                const int gi = i0 + lx;
-                if (A.bcx && (gi < 0 || gi >= A.nx)) continue;
+    if constexpr (DELTA) {
+        // f(ref_upper) - f(ref_lower) on every face with two elements
+        constexpr int NSX = TY * (TX + 1), NSY = (TY + 1) * TX;
+        for (int t = tid; t < NSX + NSY; t += NT) {
+            const bool xdir = t < NSX;
+            const int r0 = xdir ? t : t - NSX;
+            const int pos = xdir ? r0 / (TX + 1) : r0 % TX;  // row (x) / column (y)
+            const int f = xdir ? r0 % (TX + 1) : r0 / TX;    // face along the line
+            if (pos >= (xdir ? TYe : TXe) || f > (xdir ? TXe : TYe)) continue;
+            const int gf = xdir ? i0 + f : j0 + f;
+            const bool wall = xdir ? A.bcx : A.bcy;
+            if (wall && (gf == 0 || gf == (xdir ? A.nx : A.ny))) continue;
+            const Ref<T> lo = xdir ? load_ref(f - 1, pos) : load_ref(pos, f - 1);
+            T dd[V], s[V];
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
+            for (int v = 0; v < V; ++v) dd[v] = (xdir ? rfS[L::rf(v, f, pos)] : rfS[L::rf(v, pos, f)]) - lo.q[v];
+            if (xdir) dflux<EQ, 0>(lo, dd, A.ph, s);
+            else dflux<EQ, 1>(lo, dd, A.ph, s);
 #pragma unroll
-                    for (int l = 0; l < N; ++l) col[l] = sq[L::sq(v, ly + 1, lx + 1, kk * N + l)];
-                    if (side) xL[L::xs(v, ly, TXe, kk)] = line_dot<N>(tb.lm, col);
-                    else xR[L::xs(v, ly, 0, kk)] = line_dot<N>(tb.lp, col);
-                }
-            } else {
-                const int r0 = task - nxh;
-                const int side = r0 / (TXe * N), r = r0 % (TXe * N);
-                const int lx = r / N, kk = r % N;
-                const int ly = side ? TYe : -1;
-                const int gj = j0 + ly;
-                if (A.bcy && (gj < 0 || gj >= A.ny)) continue;
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-#pragma unroll
-                    for (int l = 0; l < N; ++l) col[l] = sq[L::sq(v, ly + 1, lx + 1, l * N + kk)];
-                    if (side) yB[L::ys(v, TYe, lx, kk)] = line_dot<N>(tb.lm, col);
-                    else yT[L::ys(v, 0, lx, kk)] = line_dot<N>(tb.lp, col);
-                }
-            }
+            for (int v = 0; v < V; ++v) shS[xdir ? L::shx(v, pos, f) : L::shy(v, f, pos)] = s[v];
         }
     }
     __syncthreads();
 
     // ---- phase 3: common flux, one evaluation per face point --------------
+    // A wall (transmissive edge of the domain) takes the own edge state as the
+    // ghost state and the own element as the reference.
     {
-        const int nxf = TYe * (TXe + 1) * N, nyf = TXe * (TYe + 1) * N;
-        for (int task = tid; task < nxf + nyf; task += NT) {
-            T qm[V], qp[V], F[V];
-            if (task < nxf) {
-                const int ly = task / ((TXe + 1) * N), r = task % ((TXe + 1) * N);
-                const int f = r / N, kk = r % N;
-                const int gf = i0 + f;  // global face: between elements gf-1 and gf
-                const bool left_wall = A.bcx && gf == 0, right_wall = A.bcx && gf == A.nx;
+        constexpr int NXF = TY * (TX + 1) * N, NYF = TX * (TY + 1) * N;
+        for (int t = tid; t < NXF + NYF; t += NT) {
+            const bool xdir = t < NXF;
+            const int r0 = xdir ? t : t - NXF;
+            const int line = xdir ? (TX + 1) * N : (TY + 1) * N;
+            const int pos = r0 / line, r = r0 % line;
+            const int f = r / N, kk = r % N;
+            if (pos >= (xdir ? TYe : TXe) || f > (xdir ? TXe : TYe)) continue;
+            const int gf = xdir ? i0 + f : j0 + f;
+            const bool wall = xdir ? A.bcx : A.bcy;
+            const bool lo_wall = wall && gf == 0, hi_wall = wall && gf == (xdir ? A.nx : A.ny);
+            T dm[V], dp[V], G[V];
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    T a = left_wall ? T(0) : xR[L::xs(v, ly, f, kk)];
-                    T b = right_wall ? T(0) : xL[L::xs(v, ly, f, kk)];
-                    qm[v] = left_wall ? b : a;
-                    qp[v] = right_wall ? a : b;
+            for (int v = 0; v < V; ++v) {
+                const T a = xdir ? xR[L::xs(v, pos, f, kk)] : yT[L::ys(v, f, pos, kk)];
+                const T b = xdir ? xL[L::xs(v, pos, f, kk)] : yB[L::ys(v, f, pos, kk)];
+                dm[v] = lo_wall ? b : a;
+                dp[v] = hi_wall ? a : b;
+            }
+            if constexpr (DELTA) {
+                // lower reference (the upper element at a low wall); the
+                // upper state is moved to it through the reference difference
+                const int ref_f = lo_wall ? f : f - 1;
+                const Ref<T> ref = xdir ? load_ref(ref_f, pos) : load_ref(pos, ref_f);
+                if (!lo_wall && !hi_wall) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        dp[v] += (xdir ? rfS[L::rf(v, f, pos)] : rfS[L::rf(v, pos, f)]) - ref.q[v];
                 }
-                common_flux<EQ, FLUX, 0>(qm, qp, A.ph, F);
-#pragma unroll
-                for (int v = 0; v < V; ++v) xF[L::xs(v, ly, f, kk)] = F[v];
+                if (xdir) common_flux_delta<EQ, FLUX, 0>(ref, dm, dp, A.ph, G);
+                else common_flux_delta<EQ, FLUX, 1>(ref, dm, dp, A.ph, G);
             } else {
-                const int r0 = task - nxf;
-                const int lx = r0 / ((TYe + 1) * N), r = r0 % ((TYe + 1) * N);
-                const int gl = r / N, kk = r % N;
-                const int gg = j0 + gl;
-                const bool bot_wall = A.bcy && gg == 0, top_wall = A.bcy && gg == A.ny;
+                if (xdir) common_flux<EQ, FLUX, 0>(dm, dp, A.ph, G);
+                else common_flux<EQ, FLUX, 1>(dm, dp, A.ph, G);
+            }
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    T a = bot_wall ? T(0) : yT[L::ys(v, gl, lx, kk)];
-                    T b = top_wall ? T(0) : yB[L::ys(v, gl, lx, kk)];
-                    qm[v] = bot_wall ? b : a;
-                    qp[v] = top_wall ? a : b;
-                }
-                common_flux<EQ, FLUX, 1>(qm, qp, A.ph, F);
-#pragma unroll
-                for (int v = 0; v < V; ++v) yG[L::ys(v, gl, lx, kk)] = F[v];
+            for (int v = 0; v < V; ++v) {
+                if (xdir) xF[L::xs(v, pos, f, kk)] = G[v];
+                else yG[L::ys(v, f, pos, kk)] = G[v];
             }
         }
     }
     __syncthreads();
 
-    // ---- phase 4: correction along eta, y-part of R -----------------------
+    // shift of the common flux on the low faces to the own reference
+    const bool lwall = A.bcx && i0 + tx == 0, bwall = A.bcy && j0 + ty == 0;
+
+    // ---- phase 4: y-part of R into the accumulator ------------------------
     if (valid) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            const T JB = yG[L::ys(v, ty, tx, k)] - gB[v];
+            const T sB = (DELTA && !bwall) ? shS[L::shy(v, ty, tx)] : T(0);
+            const T JB = (yG[L::ys(v, ty, tx, k)] - sB) - gB[v];
             const T JT = yG[L::ys(v, ty + 1, tx, k)] - gT[v];
 #pragma unroll
             for (int b = 0; b < N; ++b) {
                 T ys = ry[b][v] + JB * tb.dgl[b];
                 ys = ys + JT * tb.dgr[b];
-                ryS[(v * TX * TY + el) * NN + b * N + k] = -A.rhy2 * ys;
+                rS[L::sq(v, el, b * N + k)] = -A.rhy2 * ys;
             }
         }
     }
     __syncthreads();
 
-    // ---- phase 5: correction along xi, stage update, store ------------------
+    // ---- phase 5: x-part of R, stage update, store --------------------------
     T o[N][V];
     if (valid) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            const T JL = xF[L::xs(v, ty, tx, k)] - fL[v];
+            const T sL = (DELTA && !lwall) ? shS[L::shx(v, ty, tx)] : T(0);
+            const T JL = (xF[L::xs(v, ty, tx, k)] - sL) - fL[v];
             const T JR = xF[L::xs(v, ty, tx + 1, k)] - fR[v];
+            T acc[N];
+            sm_load_row<N>(rS + L::sq(v, el, k * N), acc);
 #pragma unroll
             for (int a = 0; a < N; ++a) {
                 T xs = rx[a][v] + JL * tb.dgl[a];
                 xs = xs + JR * tb.dgr[a];
-                o[a][v] = -A.rhx2 * xs + ryS[(v * TX * TY + el) * NN + k * N + a];
+                o[a][v] = acc[a] - A.rhx2 * xs;
             }
         }
-        if (A.mode >= 1) {
+        const long long off = e * NN + k * N;
+        if (A.mode == MODE_RESIDUAL) {
+        } else if (A.mode <= MODE_SO3) {
             const T dt = T(A.ctrl->dt);
-            if (A.mode == 1) {
+            const T cA = A.mode == MODE_SO2 ? T(0.75) : T(1.0 / 3.0);
+            const T cB = A.mode == MODE_SO1 ? T(1) : (A.mode == MODE_SO2 ? T(0.25) : T(2.0 / 3.0));
 #pragma unroll
-                for (int a = 0; a < N; ++a)
+            for (int v = 0; v < V; ++v) {
+                T qs[N], qn[N];
+                sm_load_row<N>(sq + L::sq(v, el, k * N), qs);
+                if (A.mode == MODE_SO1) {
 #pragma unroll
-                    for (int v = 0; v < V; ++v) o[a][v] = q[a][v] + dt * o[a][v];
-            } else {
-                T qn[N][V];
-                load_row<N, V>(A.qn + e * NN + k * N, A.npts, qn);
-                const T cA = A.mode == 2 ? T(0.75) : T(1.0 / 3.0);
-                const T cB = A.mode == 2 ? T(0.25) : T(2.0 / 3.0);
+                    for (int a = 0; a < N; ++a) o[a][v] = qs[a] + dt * o[a][v];
+                } else {
+                    gload_row<N>(A.qn + v * A.npts + off, qn);
 #pragma unroll
-                for (int a = 0; a < N; ++a)
+                    for (int a = 0; a < N; ++a) o[a][v] = cA * qn[a] + cB * (qs[a] + dt * o[a][v]);
+                }
+            }
+        } else {
+            const T dt = T(A.ctrl->dt);
 #pragma unroll
-                    for (int v = 0; v < V; ++v) o[a][v] = cA * qn[a][v] + cB * (q[a][v] + dt * o[a][v]);
+            for (int v = 0; v < V; ++v) {
+                if (A.mode == MODE_INC1) {
+#pragma unroll
+                    for (int a = 0; a < N; ++a) o[a][v] = dt * o[a][v];
+                } else {
+                    T b[N];
+                    gload_row<N>(A.qb + v * A.npts + off, b);
+                    if (A.mode == MODE_INC2) {
+#pragma unroll
+                        for (int a = 0; a < N; ++a) o[a][v] = T(0.25) * (b[a] + dt * o[a][v]);
+                    } else {
+                        T hi[N], lo[N];
+                        gload_row<N>(A.qs + v * A.npts + off, hi);
+                        gload_row<N>(A.lo + v * A.npts + off, lo);
+#pragma unroll
+                        for (int a = 0; a < N; ++a) {
+                            compensated_add(hi[a], lo[a], T(2.0 / 3.0) * (b[a] + dt * o[a][v]));
+                            o[a][v] = hi[a];
+                        }
+                        gstore_row<N>(A.lo + v * A.npts + off, lo);
+                    }
+                }
             }
         }
-        store_row<N, V>(A.out + e * NN + k * N, A.npts, o);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            T row[N];
+#pragma unroll
+            for (int a = 0; a < N; ++a) row[a] = o[a][v];
+            gstore_row<N>(A.out + v * A.npts + off, row);
+        }
     }
 
     // ---- fused element averages (Algorithm 9) -----------------------------

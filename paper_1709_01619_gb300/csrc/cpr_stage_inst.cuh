@@ -35,7 +35,7 @@ static cudaError_t stage_one(const LaunchCfg& c, const StageArgs<T>& A, int ctas
     constexpr int N = P + 1, V = NVars<EQ>::value;
     constexpr int NT = kTileX * kTileY * N;
     const size_t smem = sizeof(T) * StageLayout<N, V, kTileX, kTileY>::TOTAL;
-    auto kern = cpr_stage_kernel<T, P, EQ, DIV, FLUX, kTileX, kTileY>;
+    auto kern = cpr_stage_kernel<T, P, EQ, DIV, FLUX, kTileX, kTileY, sizeof(T) == 4>;
     if (prep) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<ctas, NT, smem, s>>>(A);
     return cudaGetLastError();
@@ -56,14 +56,15 @@ static cudaError_t stage_dispatch(const LaunchCfg& c, const StageArgs<T>& A, int
 }
 
 template <class T>
-static StageArgs<T> make_stage_args(const LaunchCfg& c, int mode, const void* qs, const void* qn, void* out,
-                                    void* avg, bool do_wave)
+static StageArgs<T> make_stage_args(const LaunchCfg& c, int mode, const StagePtrs& b, bool do_wave)
 {
     StageArgs<T> A;
-    A.qs = static_cast<const T*>(qs);
-    A.qn = static_cast<const T*>(qn);
-    A.out = static_cast<T*>(out);
-    A.avg = static_cast<T*>(avg);
+    A.qs = static_cast<const T*>(b.qs);
+    A.qb = static_cast<const T*>(b.qb);
+    A.qn = static_cast<const T*>(b.qn);
+    A.out = static_cast<T*>(b.out);
+    A.lo = static_cast<T*>(b.lo);
+    A.avg = static_cast<T*>(b.avg);
     A.wave = static_cast<T*>(c.wave);
     A.ctrl = c.ctrl;
     A.npts = c.npts;
@@ -73,7 +74,7 @@ static StageArgs<T> make_stage_args(const LaunchCfg& c, int mode, const void* qs
     A.bcy = c.bcy;
     A.tiles_x = (c.nx + kTileX - 1) / kTileX;
     A.mode = mode;
-    A.do_avg = avg != nullptr;
+    A.do_avg = b.avg != nullptr;
     A.do_wave = do_wave;
     A.rhx2 = T(2.0 / c.hx);
     A.rhy2 = T(2.0 / c.hy);
@@ -85,23 +86,22 @@ static StageArgs<T> make_stage_args(const LaunchCfg& c, int mode, const void* qs
 }
 
 template <class T, int P>
-cudaError_t launch_stage_p(const LaunchCfg& c, int mode, const void* qs, const void* qn, void* out, void* avg,
-                           bool do_wave, cudaStream_t s)
+cudaError_t launch_stage_p(const LaunchCfg& c, int mode, const StagePtrs& b, bool do_wave, cudaStream_t s)
 {
-    StageArgs<T> A = make_stage_args<T>(c, mode, qs, qn, out, avg, do_wave);
+    StageArgs<T> A = make_stage_args<T>(c, mode, b, do_wave);
     return stage_dispatch<T, P>(c, A, stage_ctas(c), s, false);
 }
 
 template <class T, int P>
 cudaError_t prepare_stage_p(const LaunchCfg& c)
 {
-    StageArgs<T> A = make_stage_args<T>(c, 0, nullptr, nullptr, nullptr, nullptr, false);
+    StagePtrs b{};
+    StageArgs<T> A = make_stage_args<T>(c, 0, b, false);
     return stage_dispatch<T, P>(c, A, 0, 0, true);
 }
 
 }  // namespace cpr
 
 #define CPR_INSTANTIATE_STAGE(T, P)                                                                     \
-    template cudaError_t cpr::launch_stage_p<T, P>(const LaunchCfg&, int, const void*, const void*, void*, \
-                                                   void*, bool, cudaStream_t);                         \
+    template cudaError_t cpr::launch_stage_p<T, P>(const LaunchCfg&, int, const StagePtrs&, bool, cudaStream_t); \
     template cudaError_t cpr::prepare_stage_p<T, P>(const LaunchCfg&);

@@ -203,6 +203,39 @@ def test_cfl_steps_land_on_t_end():
     assert rel_l2(q, q_or) <= TOL64
 
 
+@pytest.mark.parametrize("nsteps", [1, 2, 3, 7, 8, 9, 17])
+def test_fp32_increment_form_step_counts(nsteps):
+    """FP32 runs without the limiter use the increment form of SSP-RK3 with a
+    compensated state whose high part alternates between two buffers: every
+    step count, odd or even, around the 8-step graph, lands in the caller's
+    array and matches the FP64 oracle."""
+    c, o = make(dtype=nat.F32, eqn=nat.EULER, nx=19, ny=13, p=3, x1=10.0, y1=7.0, cfl=0.08)
+    x, y = oracle.point_coords(o)
+    q0 = inputs.vortex(x, y, eps=5.0, xc=5.0, yc=3.5, ly=7.0).astype(np.float32).astype(np.float64)
+    q_or, _, _ = oracle.run(o, q0, nsteps, 0.01)
+    with nat.Context(c) as ctx:
+        qd = to_dev(q0, c)
+        ctx.step(qd, nsteps, 0.01)
+        q = host(qd)
+        assert ctx.get_time()[1] == nsteps
+    assert rel_l2(q, q_or) <= 1e-6
+
+
+def test_fp32_cfl_run_to_t_end():
+    c, o = make(dtype=nat.F32, eqn=nat.EULER, nx=24, ny=20, p=3, x1=10.0, y1=10.0, cfl=0.08)
+    x, y = oracle.point_coords(o)
+    q0 = inputs.vortex(x, y, eps=5.0).astype(np.float32).astype(np.float64)
+    t_end = 0.25
+    q_or, n_or, _ = oracle.run(o, q0, 10000, 0.0, t_end)
+    with nat.Context(c) as ctx:
+        qd = to_dev(q0, c)
+        ctx.step(qd, n_or + 5, 0.0, t_end)
+        q = host(qd)
+        t, steps = ctx.get_time()
+    assert t == t_end and steps == n_or
+    assert rel_l2(q, q_or) <= 1e-6
+
+
 def test_step_host_equals_step():
     c, o = make(eqn=nat.EULER, nx=19, ny=13, p=3, x1=10.0, y1=7.0, cfl=0.08)
     q0 = rough_state(o, 4, noise=0.0)
