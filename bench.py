@@ -14,10 +14,11 @@ averages against the exact solution (which at t = 10 equals the initial field).
 summed over ranks (each rank solves its own replica; no data-path collective).
 L2 is flushed (a 256 MiB write) before every timed solve, outside its events.
 The roofline object covers the dominant kernel (the fused residual + RK stage
-kernel): algorithmic bytes per launch (read q_s, read q^n in stages 2-3, write
-the stage result: 8/3 * 4 variables * 4 B per point on average) over its mean
-launch duration; a second roofline block repeats this on a 1024 x 1024 vortex
-whose state (268 MB per array) is larger than L2.
+kernel): algorithmic bytes per launch (the FP32 increment form moves 10 state
+arrays per RK3 step -- q, B1 | q, B1, B2 | q, B2, lo, hi', lo' -- so 10/3 * 4
+variables * 4 B = 53.3 B per point and stage on average) over its mean launch
+duration; a second roofline block repeats this on a 1024 x 1024 vortex whose
+state (268 MB per array) is larger than L2.
 """
 from __future__ import annotations
 
@@ -40,6 +41,10 @@ METRIC = "CPR DOF-stage updates/s (FP32 vs FP64, equal L2 error) and % HBM roofl
 UNIT = "DOF-stage/s"
 NX, P, L, EPS, T_END, CFL = 128, 3, 10.0, 5.0, 10.0, 0.08
 HBM_NX, HBM_STEPS = 1024, 20
+# State-array reads + writes per RK3 step of the FP32 path (increment form,
+# no limiter): stage 1 reads q, writes B1; stage 2 reads q, B1, writes B2;
+# stage 3 reads q, B2 and the low part, writes the new high and low parts.
+STATE_ARRAYS_PER_STEP = 10
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -52,6 +57,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["vortex128", "vortex1024"], default="vortex128",
                     help="vortex1024: only the HBM-sized case (a short run for profiling)")
+    ap.add_argument("--quick", action="store_true",
+                    help="FP32 timed solves only (no FP64 solve, e2e, HBM case or CPU baseline)")
     return ap.parse_args()
 
 
@@ -238,7 +245,7 @@ def hbm_case(make, peak, steps=HBM_STEPS):
     msH = eh[0].elapsed_time(eh[1])
     dofH = HBM_NX * HBM_NX * (P + 1) ** 2
     launchH = msH / (3 * steps)
-    achievedH = dofH * 16 * (8.0 / 3.0) / (launchH * 1e-3) / 1e9
+    achievedH = dofH * 16 * STATE_ARRAYS_PER_STEP / 3.0 / (launchH * 1e-3) / 1e9
     ctxH.close()
     return {"workload": "euler_vortex_1024x1024_p3_fp32", "bound": "hbm", "achieved": achievedH,
             "peak": peak, "unit": "GB/s", "frac": achievedH / peak, "launch_ms": launchH,
@@ -314,8 +321,15 @@ def run_cpr(args, world, rank, local):
 
     # dominant kernel: fused residual + stage, 3 launches per RK3 step
     launch_ms = ms / (args.steps * 3 * nsteps)
-    bytes_per_launch = dof * 4 * 4 * (8.0 / 3.0)
+    bytes_per_launch = dof * 4 * 4 * STATE_ARRAYS_PER_STEP / 3.0
     achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
+
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"workload": "euler_vortex_128x128_p3_t10", "value": value, "unit": UNIT,
+                              "ms_per_step": ms_max / args.steps, "rk3_steps": nsteps,
+                              "launch_ms": launch_ms}), flush=True)
+        return
 
     # ---- e2e through the host-buffer entry point ------------------------------
     qh_in = q0_32.cpu().pin_memory()

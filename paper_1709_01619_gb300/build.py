@@ -45,7 +45,7 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
         return LIB
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
-    extra = list(extra or [])
+    extra = list(extra or []) + os.environ.get("CPR_NVCC_FLAGS", "").split()
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")

@@ -34,7 +34,15 @@ struct LaunchCfg {
     double* partials;  // norms partials
 };
 
-constexpr int kTileX = 8, kTileY = 8;
+// Element tile of one stage-kernel CTA (compile-time; overridable for tuning
+// sweeps with -DCPR_TILE_X=.. -DCPR_TILE_Y=..).
+#ifndef CPR_TILE_X
+#define CPR_TILE_X 8
+#endif
+#ifndef CPR_TILE_Y
+#define CPR_TILE_Y 8
+#endif
+constexpr int kTileX = CPR_TILE_X, kTileY = CPR_TILE_Y;
 
 inline int stage_ctas(const LaunchCfg& c)
 {

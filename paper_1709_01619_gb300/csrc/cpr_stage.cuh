@@ -29,13 +29,15 @@
 // fluxes directly (reference zero).
 //
 // Phases (one barrier after each):
-//   1 rows of the stage state into registers and shared memory, element
-//     references; halo lines (the edge states of the neighbour elements
-//     facing the tile) straight from L2
-//   2 x-lines and y-lines: flux differences, d/dxi and d/deta, edge states;
-//     reference shift of every face
-//   3 common flux on every face point of the tile (one evaluation per face)
-//   4 y-lines: y-part of R (shared accumulator)
+//   1 rows of the stage state into shared memory, element references; halo
+//     lines (the edge states of the neighbour elements facing the tile)
+//     straight from L2
+//   2 x-lines and y-lines: flux differences, d/dxi and d/deta, edge states,
+//     flux shifts to the left and lower neighbours' references
+//   3 each thread: common flux on its element's left and lower face point
+//     (plus the right / upper face for the tile's last column / row), one
+//     evaluation per face point; the neighbour's copy goes to shared memory
+//   4 y-lines: y-part of R into a shared accumulator (over the dead tile copy)
 //   5 x-lines: x-part of R, stage update, store; optional fused element
 //     averages (Algorithm 9) and max signal speed of the result.
 #pragma once
@@ -74,21 +76,24 @@ struct StageLayout {
     static constexpr int ES = (NN % 4 == 0) ? NN + 4 : ((NN + 3) / 4) * 4;
     static constexpr int E = TX * TY;
     static constexpr int PE = (TX + 2) * (TY + 2);     // tile with its halo ring
-    static constexpr int NR = 8;                       // reference: q[4], u, v, p, H
-    static constexpr int SQ = V * E * ES;              // tile copy of the stage state
-    static constexpr int RS = V * E * ES;              // residual accumulator
-    static constexpr int XS = V * TY * (TX + 1) * N;   // one x-face array
-    static constexpr int YS = V * (TY + 1) * TX * N;   // one y-face array
-    static constexpr int RF = NR * PE;                 // element references
-    static constexpr int SH = V * (TY * (TX + 1) + (TY + 1) * TX);  // face shifts
-    static constexpr int TOTAL = SQ + RS + 3 * XS + 3 * YS + RF + SH;
+    static constexpr int SQ = V * E * ES;              // tile copy; later the y-part of R
+    static constexpr int XR = V * TY * (TX + 1) * N;   // right edge states, elements -1..TX-1
+    static constexpr int XH = V * TY * N;              // left edge states of the right halo
+    static constexpr int XG = V * TY * TX * N;         // common flux for the left element
+    static constexpr int YT = V * (TY + 1) * TX * N;
+    static constexpr int YH = V * TX * N;
+    static constexpr int YG = V * TY * TX * N;
+    static constexpr int RF = V * PE;                  // element reference states
+    static constexpr int TOTAL = SQ + XR + XH + XG + YT + YH + YG + RF;
     __device__ static int sq(int v, int el, int pt) { return (v * E + el) * ES + pt; }
-    __device__ static int xs(int v, int ty, int f, int k) { return ((v * TY + ty) * (TX + 1) + f) * N + k; }
-    __device__ static int ys(int v, int g, int tx, int k) { return ((v * (TY + 1) + g) * TX + tx) * N + k; }
+    __device__ static int xr(int v, int ty, int f, int k) { return ((v * TY + ty) * (TX + 1) + f) * N + k; }
+    __device__ static int xh(int v, int ty, int k) { return (v * TY + ty) * N + k; }
+    __device__ static int xg(int v, int ty, int tx, int k) { return ((v * TY + ty) * TX + tx) * N + k; }
+    __device__ static int yt(int v, int g, int tx, int k) { return ((v * (TY + 1) + g) * TX + tx) * N + k; }
+    __device__ static int yh(int v, int tx, int k) { return (v * TX + tx) * N + k; }
+    __device__ static int yg(int v, int ty, int tx, int k) { return ((v * TY + ty) * TX + tx) * N + k; }
     // reference of the element at tile coordinates (lx, ly), -1 <= lx <= TX
-    __device__ static int rf(int c, int lx, int ly) { return c * PE + (ly + 1) * (TX + 2) + (lx + 1); }
-    __device__ static int shx(int v, int ty, int f) { return (v * TY + ty) * (TX + 1) + f; }
-    __device__ static int shy(int v, int g, int tx) { return V * TY * (TX + 1) + (v * (TY + 1) + g) * TX + tx; }
+    __device__ static int rf(int v, int lx, int ly) { return v * PE + (ly + 1) * (TX + 2) + (lx + 1); }
 };
 
 // Edge value of a line of N values: sum_l c_l x_l, in one fixed fma order so
@@ -172,6 +177,16 @@ __device__ __forceinline__ void line_flux(const Ref<T>& r, const T* d, const Phy
     else flux_y<EQ>(d, ph, out);
 }
 
+// Common flux through an x-face (DIR 0) or y-face (DIR 1) between the lower
+// state dm and the upper state dp: relative to the reference in the delta
+// form (F* - f(ref)), the flux itself otherwise.
+template <int EQ, int FLUX, int DIR, bool DELTA, class T>
+__device__ __forceinline__ void face_flux(const Ref<T>& r, const T* dm, const T* dp, const Phys<T>& ph, T* G)
+{
+    if constexpr (DELTA) common_flux_delta<EQ, FLUX, DIR>(r, dm, dp, ph, G);
+    else common_flux<EQ, FLUX, DIR>(dm, dp, ph, G);
+}
+
 // q' = hi + lo + D as hi' + lo' (Knuth's two-sum of hi and D, then the old
 // and new low parts folded back); the pair keeps about 48 bits.
 __device__ __forceinline__ void compensated_add(float& hi, float& lo, float D)
@@ -192,10 +207,13 @@ __device__ __forceinline__ void compensated_add(double& hi, double& lo, double D
 
 // Resident CTAs per SM the register budget is sized for (FP32: as many as the
 // shared memory allows; FP64: one).
+#ifndef CPR_STAGE_MINB_FP32
+#define CPR_STAGE_MINB_FP32 3
+#endif
 template <class T, int N>
 constexpr int stage_min_blocks()
 {
-    return sizeof(T) == 8 ? 1 : (N <= 3 ? 3 : 2);
+    return sizeof(T) == 8 ? 1 : (N <= 4 ? CPR_STAGE_MINB_FP32 : 2);
 }
 
 template <class T, int P, int EQ, int DIV, int FLUX, int TX, int TY, bool DELTA>
@@ -207,16 +225,15 @@ cpr_stage_kernel(const StageArgs<T> A)
     using L = StageLayout<N, V, TX, TY>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sq = reinterpret_cast<T*>(smem_raw);
-    T* rS = sq + L::SQ;  // residual accumulator, same layout as sq
-    T* xL = rS + L::RS;  // left edge state (delta) of elements 0..TXe (index = element)
-    T* xR = xL + L::XS;  // right edge state of elements -1..TXe-1 (index = element + 1)
-    T* xF = xR + L::XS;  // common flux minus f(lower reference) on x-faces 0..TXe
-    T* yB = xF + L::XS;
-    T* yT = yB + L::YS;
-    T* yG = yT + L::YS;
-    T* rfS = yG + L::YS; // element references over the tile and its halo ring
-    T* shS = rfS + L::RF;
-    T* avS = xL;         // row partial sums of the averages, reuses xL after phase 3
+    T* rS = sq;          // y-part of R, once the tile copy is dead
+    T* xR = sq + L::SQ;
+    T* xH = xR + L::XR;
+    T* xG = xH + L::XH;
+    T* yT = xG + L::XG;
+    T* yH = yT + L::YT;
+    T* yG = yH + L::YH;
+    T* rfS = yG + L::YG;
+    T* avS = xR;         // row partial sums of the averages, reuses xR after phase 4
 
     if (A.mode > 0 && A.ctrl->done) return;  // t_end reached: uniform exit
 
@@ -299,60 +316,35 @@ cpr_stage_kernel(const StageArgs<T> A)
                 for (int l = 0; l < N; ++l) line[l] -= ref;
                 const T d = line_dot<N>(coef, line);
                 if (xdir) {
-                    if (side) xL[L::xs(v, pos, TXe, kk)] = d;
-                    else xR[L::xs(v, pos, 0, kk)] = d;
+                    if (side) xH[L::xh(v, pos, kk)] = d;
+                    else xR[L::xr(v, pos, 0, kk)] = d;
                 } else {
-                    if (side) yB[L::ys(v, TYe, pos, kk)] = d;
-                    else yT[L::ys(v, 0, pos, kk)] = d;
+                    if (side) yH[L::yh(v, pos, kk)] = d;
+                    else yT[L::yt(v, 0, pos, kk)] = d;
                 }
                 if (DELTA && kk == 0) rfS[L::rf(v, lx, ly)] = ref;
             }
         }
     }
     __syncthreads();
-    // derived reference quantities (u, v, p, H) of every element in reach
-    if constexpr (DELTA && EQ == EQ_EULER) {
-        for (int c = tid; c < L::PE; c += NT) {
-            const int lx = c % (TX + 2) - 1, ly = c / (TX + 2) - 1;
-            const bool tile = lx >= 0 && lx < TXe && ly >= 0 && ly < TYe;
-            const bool xh = (lx == -1 || lx == TXe) && ly >= 0 && ly < TYe;
-            const bool yh = (ly == -1 || ly == TYe) && lx >= 0 && lx < TXe;
-            if (!(tile || xh || yh)) continue;
-            const int gi = i0 + lx, gj = j0 + ly;
-            if ((A.bcx && (gi < 0 || gi >= A.nx)) || (A.bcy && (gj < 0 || gj >= A.ny))) continue;
-            T q0[4];
-#pragma unroll
-            for (int v = 0; v < 4; ++v) q0[v] = rfS[L::rf(v, lx, ly)];
-            const Ref<T> r = make_ref<EQ>(q0, A.ph);
-            rfS[L::rf(4, lx, ly)] = r.u;
-            rfS[L::rf(5, lx, ly)] = r.v;
-            rfS[L::rf(6, lx, ly)] = r.p;
-            rfS[L::rf(7, lx, ly)] = r.H;
-        }
-    }
-    __syncthreads();
 
-    auto load_ref = [&](int lx, int ly) {
-        Ref<T> r;
-#pragma unroll
-        for (int v = 0; v < 4; ++v) r.q[v] = v < V ? rfS[L::rf(v, lx, ly)] : T(0);
-        if constexpr (EQ == EQ_EULER) {
-            r.u = rfS[L::rf(4, lx, ly)];
-            r.v = rfS[L::rf(5, lx, ly)];
-            r.p = rfS[L::rf(6, lx, ly)];
-            r.H = rfS[L::rf(7, lx, ly)];
-        } else {
-            r.u = r.v = r.p = r.H = T(0);
-        }
-        return r;
-    };
+    // walls: transmissive edges of the domain (ghost state = own edge state)
+    const bool lwall = A.bcx && i0 + tx == 0, bwall = A.bcy && j0 + ty == 0;
+    const bool redge = tx == TXe - 1, tedge = ty == TYe - 1;
+    const bool rwall = A.bcx && i0 + TXe == A.nx, twall = A.bcy && j0 + TYe == A.ny;
 
-    // ---- phase 2: line operators, face shifts --------------------------------
-    Ref<T> rf;
-    T rx[N][V], ry[N][V];
-    T fL[V], fR[V], gB[V], gT[V];
+    // ---- phase 2: line operators ----------------------------------------
+    Ref<T> rf;                      // own reference (delta form)
+    T rx[N][V], ry[N][V];           // d/dxi, d/deta of the flux differences
+    T fL[V], fR[V], gB[V], gT[V];   // edge values of the flux
+    T eL[V], eB[V];                 // own left / bottom edge states
+    T sL[V], sB[V];                 // f(ref_own) - f(ref_left), f(ref_own) - f(ref_below)
+    T oL[V], oB[V];                 // ref_left - ref_own, ref_below - ref_own
     if (valid) {
-        if constexpr (DELTA) rf = load_ref(tx, ty);
+        T q0[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) q0[v] = DELTA ? rfS[L::rf(v, tx, ty)] : T(0);
+        if constexpr (DELTA) rf = make_ref<EQ>(q0, A.ph);
         // x-line: row k
         T d[N][V], f[N][V], col[N];
 #pragma unroll
@@ -360,11 +352,11 @@ cpr_stage_kernel(const StageArgs<T> A)
             T row[N];
             sm_load_row<N>(sq + L::sq(v, el, k * N), row);
 #pragma unroll
-            for (int a = 0; a < N; ++a) d[a][v] = DELTA ? row[a] - rf.q[v] : row[a];
+            for (int a = 0; a < N; ++a) d[a][v] = DELTA ? row[a] - q0[v] : row[a];
         }
 #pragma unroll
         for (int a = 0; a < N; ++a) line_flux<EQ, 0, DELTA>(rf, d[a], A.ph, f[a]);
-        T eL[V], eR[V];
+        T eR[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
 #pragma unroll
@@ -391,7 +383,7 @@ cpr_stage_kernel(const StageArgs<T> A)
 #pragma unroll
                     for (int l = 0; l < N; ++l) col[l] = d[l][v];
                     dq[v] = line_dot<N>(tb.D[a], col);
-                    qa[v] = DELTA ? rf.q[v] + d[a][v] : d[a][v];
+                    qa[v] = DELTA ? q0[v] + d[a][v] : d[a][v];
                 }
                 flux_jvp<EQ, 0>(qa, dq, A.ph, rx[a]);
             }
@@ -399,21 +391,18 @@ cpr_stage_kernel(const StageArgs<T> A)
             line_flux<EQ, 0, DELTA>(rf, eR, A.ph, fR);
         }
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            xL[L::xs(v, ty, tx, k)] = eL[v];
-            xR[L::xs(v, ty, tx + 1, k)] = eR[v];
-        }
+        for (int v = 0; v < V; ++v) xR[L::xr(v, ty, tx + 1, k)] = eR[v];
         // y-line: column k
 #pragma unroll
         for (int b = 0; b < N; ++b)
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const T x = sq[L::sq(v, el, b * N + k)];
-                d[b][v] = DELTA ? x - rf.q[v] : x;
+                d[b][v] = DELTA ? x - q0[v] : x;
             }
 #pragma unroll
         for (int b = 0; b < N; ++b) line_flux<EQ, 1, DELTA>(rf, d[b], A.ph, f[b]);
-        T eB[V], eT[V];
+        T eT[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
 #pragma unroll
@@ -440,7 +429,7 @@ cpr_stage_kernel(const StageArgs<T> A)
 #pragma unroll
                     for (int l = 0; l < N; ++l) col[l] = d[l][v];
                     dq[v] = line_dot<N>(tb.D[b], col);
-                    qb[v] = DELTA ? rf.q[v] + d[b][v] : d[b][v];
+                    qb[v] = DELTA ? q0[v] + d[b][v] : d[b][v];
                 }
                 flux_jvp<EQ, 1>(qb, dq, A.ph, ry[b]);
             }
@@ -448,97 +437,87 @@ cpr_stage_kernel(const StageArgs<T> A)
             line_flux<EQ, 1, DELTA>(rf, eT, A.ph, gT);
         }
 #pragma unroll
+        for (int v = 0; v < V; ++v) yT[L::yt(v, ty + 1, tx, k)] = eT[v];
+        // reference offsets and flux shifts to the left and lower neighbours:
+        // f(ref_own) - f(ref_nb) = -(f(ref_own + (ref_nb - ref_own)) - f(ref_own))
+        if constexpr (DELTA) {
+            T t[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                oL[v] = lwall ? T(0) : rfS[L::rf(v, tx - 1, ty)] - q0[v];
+                oB[v] = bwall ? T(0) : rfS[L::rf(v, tx, ty - 1)] - q0[v];
+            }
+            dflux<EQ, 0>(rf, oL, A.ph, t);
+#pragma unroll
+            for (int v = 0; v < V; ++v) sL[v] = -t[v];
+            dflux<EQ, 1>(rf, oB, A.ph, t);
+#pragma unroll
+            for (int v = 0; v < V; ++v) sB[v] = -t[v];
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) sL[v] = sB[v] = oL[v] = oB[v] = T(0);
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 3: common flux on the own left and lower faces --------------
+    // (and on the right / upper face of the tile's last column / row), all
+    // relative to the own reference; the value for the left / lower
+    // neighbour is shifted to that neighbour's reference.
+    T JL[V], JB[V], JR[V], JT[V];
+    if (valid) {
+        T dm[V], G[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) dm[v] = lwall ? eL[v] : xR[L::xr(v, ty, tx, k)] + oL[v];
+        face_flux<EQ, FLUX, 0, DELTA>(rf, dm, eL, A.ph, G);
+#pragma unroll
         for (int v = 0; v < V; ++v) {
-            yB[L::ys(v, ty, tx, k)] = eB[v];
-            yT[L::ys(v, ty + 1, tx, k)] = eT[v];
+            JL[v] = G[v] - fL[v];
+            if (tx > 0) xG[L::xg(v, ty, tx, k)] = G[v] + sL[v];
         }
-    }
-    if constexpr (DELTA) {
-        // f(ref_upper) - f(ref_lower) on every face with two elements
-        constexpr int NSX = TY * (TX + 1), NSY = (TY + 1) * TX;
-        for (int t = tid; t < NSX + NSY; t += NT) {
-            const bool xdir = t < NSX;
-            const int r0 = xdir ? t : t - NSX;
-            const int pos = xdir ? r0 / (TX + 1) : r0 % TX;  // row (x) / column (y)
-            const int f = xdir ? r0 % (TX + 1) : r0 / TX;    // face along the line
-            if (pos >= (xdir ? TYe : TXe) || f > (xdir ? TXe : TYe)) continue;
-            const int gf = xdir ? i0 + f : j0 + f;
-            const bool wall = xdir ? A.bcx : A.bcy;
-            if (wall && (gf == 0 || gf == (xdir ? A.nx : A.ny))) continue;
-            const Ref<T> lo = xdir ? load_ref(f - 1, pos) : load_ref(pos, f - 1);
-            T dd[V], s[V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) dd[v] = (xdir ? rfS[L::rf(v, f, pos)] : rfS[L::rf(v, pos, f)]) - lo.q[v];
-            if (xdir) dflux<EQ, 0>(lo, dd, A.ph, s);
-            else dflux<EQ, 1>(lo, dd, A.ph, s);
+        for (int v = 0; v < V; ++v) dm[v] = bwall ? eB[v] : yT[L::yt(v, ty, tx, k)] + oB[v];
+        face_flux<EQ, FLUX, 1, DELTA>(rf, dm, eB, A.ph, G);
 #pragma unroll
-            for (int v = 0; v < V; ++v) shS[xdir ? L::shx(v, pos, f) : L::shy(v, f, pos)] = s[v];
+        for (int v = 0; v < V; ++v) {
+            JB[v] = G[v] - gB[v];
+            if (ty > 0) yG[L::yg(v, ty, tx, k)] = G[v] + sB[v];
+        }
+        if (redge) {
+            T dp[V], eR[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                eR[v] = xR[L::xr(v, ty, tx + 1, k)];
+                dp[v] = rwall ? eR[v] : xH[L::xh(v, ty, k)] + (DELTA ? rfS[L::rf(v, tx + 1, ty)] - rf.q[v] : T(0));
+            }
+            face_flux<EQ, FLUX, 0, DELTA>(rf, eR, dp, A.ph, G);
+#pragma unroll
+            for (int v = 0; v < V; ++v) JR[v] = G[v] - fR[v];
+        }
+        if (tedge) {
+            T dp[V], eT[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                eT[v] = yT[L::yt(v, ty + 1, tx, k)];
+                dp[v] = twall ? eT[v] : yH[L::yh(v, tx, k)] + (DELTA ? rfS[L::rf(v, tx, ty + 1)] - rf.q[v] : T(0));
+            }
+            face_flux<EQ, FLUX, 1, DELTA>(rf, eT, dp, A.ph, G);
+#pragma unroll
+            for (int v = 0; v < V; ++v) JT[v] = G[v] - gT[v];
         }
     }
     __syncthreads();
-
-    // ---- phase 3: common flux, one evaluation per face point --------------
-    // A wall (transmissive edge of the domain) takes the own edge state as the
-    // ghost state and the own element as the reference.
-    {
-        constexpr int NXF = TY * (TX + 1) * N, NYF = TX * (TY + 1) * N;
-        for (int t = tid; t < NXF + NYF; t += NT) {
-            const bool xdir = t < NXF;
-            const int r0 = xdir ? t : t - NXF;
-            const int line = xdir ? (TX + 1) * N : (TY + 1) * N;
-            const int pos = r0 / line, r = r0 % line;
-            const int f = r / N, kk = r % N;
-            if (pos >= (xdir ? TYe : TXe) || f > (xdir ? TXe : TYe)) continue;
-            const int gf = xdir ? i0 + f : j0 + f;
-            const bool wall = xdir ? A.bcx : A.bcy;
-            const bool lo_wall = wall && gf == 0, hi_wall = wall && gf == (xdir ? A.nx : A.ny);
-            T dm[V], dp[V], G[V];
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const T a = xdir ? xR[L::xs(v, pos, f, kk)] : yT[L::ys(v, f, pos, kk)];
-                const T b = xdir ? xL[L::xs(v, pos, f, kk)] : yB[L::ys(v, f, pos, kk)];
-                dm[v] = lo_wall ? b : a;
-                dp[v] = hi_wall ? a : b;
-            }
-            if constexpr (DELTA) {
-                // lower reference (the upper element at a low wall); the
-                // upper state is moved to it through the reference difference
-                const int ref_f = lo_wall ? f : f - 1;
-                const Ref<T> ref = xdir ? load_ref(ref_f, pos) : load_ref(pos, ref_f);
-                if (!lo_wall && !hi_wall) {
-#pragma unroll
-                    for (int v = 0; v < V; ++v)
-                        dp[v] += (xdir ? rfS[L::rf(v, f, pos)] : rfS[L::rf(v, pos, f)]) - ref.q[v];
-                }
-                if (xdir) common_flux_delta<EQ, FLUX, 0>(ref, dm, dp, A.ph, G);
-                else common_flux_delta<EQ, FLUX, 1>(ref, dm, dp, A.ph, G);
-            } else {
-                if (xdir) common_flux<EQ, FLUX, 0>(dm, dp, A.ph, G);
-                else common_flux<EQ, FLUX, 1>(dm, dp, A.ph, G);
-            }
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                if (xdir) xF[L::xs(v, pos, f, kk)] = G[v];
-                else yG[L::ys(v, f, pos, kk)] = G[v];
-            }
-        }
-    }
-    __syncthreads();
-
-    // shift of the common flux on the low faces to the own reference
-    const bool lwall = A.bcx && i0 + tx == 0, bwall = A.bcy && j0 + ty == 0;
 
     // ---- phase 4: y-part of R into the accumulator ------------------------
     if (valid) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            const T sB = (DELTA && !bwall) ? shS[L::shy(v, ty, tx)] : T(0);
-            const T JB = (yG[L::ys(v, ty, tx, k)] - sB) - gB[v];
-            const T JT = yG[L::ys(v, ty + 1, tx, k)] - gT[v];
+            if (!redge) JR[v] = xG[L::xg(v, ty, tx + 1, k)] - fR[v];
+            if (!tedge) JT[v] = yG[L::yg(v, ty + 1, tx, k)] - gT[v];
 #pragma unroll
             for (int b = 0; b < N; ++b) {
-                T ys = ry[b][v] + JB * tb.dgl[b];
-                ys = ys + JT * tb.dgr[b];
+                T ys = ry[b][v] + JB[v] * tb.dgl[b];
+                ys = ys + JT[v] * tb.dgr[b];
                 rS[L::sq(v, el, b * N + k)] = -A.rhy2 * ys;
             }
         }
@@ -550,15 +529,12 @@ cpr_stage_kernel(const StageArgs<T> A)
     if (valid) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            const T sL = (DELTA && !lwall) ? shS[L::shx(v, ty, tx)] : T(0);
-            const T JL = (xF[L::xs(v, ty, tx, k)] - sL) - fL[v];
-            const T JR = xF[L::xs(v, ty, tx + 1, k)] - fR[v];
             T acc[N];
             sm_load_row<N>(rS + L::sq(v, el, k * N), acc);
 #pragma unroll
             for (int a = 0; a < N; ++a) {
-                T xs = rx[a][v] + JL * tb.dgl[a];
-                xs = xs + JR * tb.dgr[a];
+                T xs = rx[a][v] + JL[v] * tb.dgl[a];
+                xs = xs + JR[v] * tb.dgr[a];
                 o[a][v] = acc[a] - A.rhx2 * xs;
             }
         }
@@ -571,7 +547,7 @@ cpr_stage_kernel(const StageArgs<T> A)
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 T qs[N], qn[N];
-                sm_load_row<N>(sq + L::sq(v, el, k * N), qs);
+                gload_row<N>(A.qs + v * A.npts + off, qs);
                 if (A.mode == MODE_SO1) {
 #pragma unroll
                     for (int a = 0; a < N; ++a) o[a][v] = qs[a] + dt * o[a][v];
