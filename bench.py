@@ -252,6 +252,40 @@ def hbm_case(make, peak, steps=HBM_STEPS):
             "dof_stage_per_s": dofH * 3 * steps / (msH * 1e-3), "rk3_steps": steps}
 
 
+def batch_case(peak, steps=100, warmup=3):
+    """64 isentropic-vortex instances (N ~ U{32..256}, p ~ U{2,3,4}, strength
+    ~ U[1,5], numpy seed 0) on [0,10]^2 in FP32, advanced together by the
+    batched solver with per-instance CFL steps after autotuning."""
+    import torch
+    from paper_1709_01619_gb300 import _native as nat
+    from paper_1709_01619_gb300 import inputs
+    specs = inputs.batch_instances(64, seed=0)
+    cfgs = [nat.Config(eqn=nat.EULER, nx=s["N"], ny=s["N"], p=s["p"], x1=L, y1=L, dtype=nat.F32,
+                       cfl={2: 0.1, 3: 0.08, 4: 0.06}[s["p"]]) for s in specs]
+    qs = []
+    for c, s in zip(cfgs, specs):
+        with nat.Context(c) as ctx:
+            x, y = ctx.point_coords()
+        qs.append(torch.tensor(inputs.vortex(x, y, eps=s["eps"]), dtype=torch.float32, device="cuda"))
+    dof = sum(c.nx * c.ny * (c.p + 1) ** 2 for c in cfgs)
+    with nat.Batch(cfgs) as b:
+        choices = b.tune(qs)
+        b.step(qs, warmup)
+        torch.cuda.synchronize()
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev[0].record()
+        b.step(qs, steps)
+        ev[1].record()
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1])
+    rate = dof * 3 * steps / (ms * 1e-3)
+    achieved = rate * 16 * STATE_ARRAYS_PER_STEP / 3.0 / 1e9
+    return {"workload": "batch_64_vortex_N32-256_p2-4_fp32", "instances": len(cfgs), "dof": dof,
+            "rk3_steps": steps, "ms": ms, "dof_stage_per_s": rate, "bound": "hbm",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "tuned": [{"p": p, "family": f, "grid": g} for p, f, g in choices]}
+
+
 def run_hbm_only(args):
     import torch
     from paper_1709_01619_gb300 import _native as nat
@@ -363,6 +397,7 @@ def run_cpr(args, world, rank, local):
     del ctx64
 
     hbm = hbm_case(make, peak)
+    batch = batch_case(peak)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, s, secs, thr = oracle_sample(12.0)
@@ -385,6 +420,7 @@ def run_cpr(args, world, rank, local):
                      "kernel": "cpr_stage_kernel<float,3,Euler,LP,Rusanov>",
                      "note": "state (4.2 MB) is L2-resident at this size"},
         "roofline_hbm_case": hbm,
+        "batch": batch,
         "f64": {"value": value64, "unit": UNIT, "ms_per_solve": ms64, "rk3_steps": n64,
                 "bound": "alu"},
         "l2_rho_avg_error": {"f32": err32, "f64": err64},

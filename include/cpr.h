@@ -204,6 +204,43 @@ cpr_status cpr_residual_vjp(cpr_ctx* ctx, const void* q_dev, const void* rbar_de
 cpr_status cpr_step_vjp(cpr_ctx* ctx, const void* q_dev, const void* qbar_out_dev, void* qbar_in_dev,
                         double dt);
 
+/* ---- batches ------------------------------------------------------------
+ * Many independent problems of uneven size and order advanced together (no
+ * counterpart in the paper's single-grid runs).  For every SSP-RK3 stage
+ * there is one persistent launch per polynomial order present in the batch;
+ * each launch walks the tiles of all instances of that order.  Each
+ * instance keeps its own simulated time and CFL step.  All instances share
+ * eqn, dtype and flux; batches run Gauss points, the LP divergence and no
+ * limiter (CPR_EINVAL otherwise).  FP32 batches use the compensated
+ * increment form of the RK stages like cpr_step. */
+typedef struct cpr_batch cpr_batch;
+
+/* Create a batch of n instances (cfgs[0..n-1]) on the current device; the
+ * batch owns two stage buffers, the low part of the state (FP32), partial
+ * maxima and a control block per instance. */
+cpr_status cpr_batch_init(const cpr_config* cfgs, int n, void* stream, cpr_batch** out);
+void cpr_batch_destroy(cpr_batch* b);
+const char* cpr_batch_last_error(const cpr_batch* b);
+
+/* Advance every instance i, state q_devs[i] (layout of cfgs[i], in place),
+ * by up to nsteps SSP-RK3 steps with the semantics of cpr_step (dt_fixed,
+ * t_end apply to every instance; CFL steps are per instance).  Changing the
+ * set of q_devs pointers between calls synchronises the stream once. */
+cpr_status cpr_batch_step(cpr_batch* b, void* const* q_devs, int nsteps, double dt_fixed, double t_end);
+
+/* Autotuner: for each order group, times one RK3 step for each tile family
+ * (8x8 and 16x4 elements per CTA) and each persistent grid of 1..max
+ * resident CTAs per SM, and keeps the fastest.  The states q_devs are not
+ * modified and the simulated times are kept.  choices (nullable) receives 3
+ * ints per group: p, family, grid size; *ngroups (nullable) the group
+ * count (at most 4).  Synchronises. */
+cpr_status cpr_batch_tune(cpr_batch* b, void* const* q_devs, int* choices, int* ngroups);
+
+/* Simulated time and steps of instance i (synchronises); set the time of
+ * every instance (synchronises). */
+cpr_status cpr_batch_get_time(cpr_batch* b, int i, double* t, long long* steps);
+cpr_status cpr_batch_set_time(cpr_batch* b, double t, long long steps);
+
 /* Largest state, in bytes, that cpr_step_noalloc accepts (16 MiB). */
 #define CPR_NOALLOC_MAX_STATE_BYTES (16u << 20)
 

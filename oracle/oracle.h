@@ -103,7 +103,7 @@ int oracle_averages(const oracle_cfg* c, const double* q, double* avg);
  * receives max over edges/variables of |delta - mt(delta, D+, D-)| - eps, the
  * signed distance of the marking decision from its threshold.
  * Returns the number of marked elements.
- * Pinned by: mean preservation, no marks on linear fields, monotone 1D step. */
+ * Pinned by: mean preservation, linear fields are fixed points, no marks under a large TVB constant, monotone 1D step. */
 long oracle_limit(const oracle_cfg* c, double* q, int* marks, double* margin);
 
 /* Largest signal speed over all solution points: sqrt(u^2+v^2)+c (Euler) or

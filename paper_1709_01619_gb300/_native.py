@@ -33,7 +33,8 @@ EXPORTS = (
     "cpr_init", "cpr_destroy", "cpr_state_elems", "cpr_last_error", "cpr_point_coords",
     "cpr_residual", "cpr_step", "cpr_step_host", "cpr_limit", "cpr_get_marks", "cpr_averages",
     "cpr_norms", "cpr_set_time", "cpr_get_time", "cpr_residual_vjp", "cpr_step_vjp",
-    "cpr_step_noalloc",
+    "cpr_step_noalloc", "cpr_batch_init", "cpr_batch_destroy", "cpr_batch_last_error",
+    "cpr_batch_step", "cpr_batch_tune", "cpr_batch_get_time", "cpr_batch_set_time",
 )
 
 
@@ -161,6 +162,20 @@ def load():
             lib.cpr_residual_vjp.argtypes = [P, P, P, P]
             lib.cpr_step_vjp.restype = I
             lib.cpr_step_vjp.argtypes = [P, P, P, P, D]
+            lib.cpr_batch_init.restype = I
+            lib.cpr_batch_init.argtypes = [ctypes.POINTER(_Config), I, P, ctypes.POINTER(P)]
+            lib.cpr_batch_destroy.restype = None
+            lib.cpr_batch_destroy.argtypes = [P]
+            lib.cpr_batch_last_error.restype = ctypes.c_char_p
+            lib.cpr_batch_last_error.argtypes = [P]
+            lib.cpr_batch_step.restype = I
+            lib.cpr_batch_step.argtypes = [P, ctypes.POINTER(P), I, D, D]
+            lib.cpr_batch_tune.restype = I
+            lib.cpr_batch_tune.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(I), ctypes.POINTER(I)]
+            lib.cpr_batch_get_time.restype = I
+            lib.cpr_batch_get_time.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(LL)]
+            lib.cpr_batch_set_time.restype = I
+            lib.cpr_batch_set_time.argtypes = [P, D, LL]
             _lib = lib
     return _lib
 
@@ -301,6 +316,78 @@ class Context:
     def close(self):
         if getattr(self, "h", None):
             self.lib.cpr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Many CPR problems advanced together (wraps ``cpr_batch``)."""
+
+    def __init__(self, cfgs, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the CPR kernels need a CUDA device")
+        self.lib = load()
+        self.cfgs = list(cfgs)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        arr = (_Config * len(self.cfgs))(*[c._c() for c in self.cfgs])
+        h = ctypes.c_void_p()
+        st = self.lib.cpr_batch_init(arr, len(self.cfgs), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        if st != CPR_OK:
+            raise CprError(st, self.lib.cpr_batch_last_error(None).decode())
+        self.h = h
+
+    def _check(self, st):
+        if st != CPR_OK:
+            raise CprError(st, self.lib.cpr_batch_last_error(self.h).decode())
+
+    def _ptrs(self, qs):
+        if len(qs) != len(self.cfgs):
+            raise ValueError("one state per instance")
+        for q, c in zip(qs, self.cfgs):
+            if q.device.type != "cuda" or q.dtype != c.torch_dtype or not q.is_contiguous() \
+                    or q.numel() != c.nvars * c.ne * (c.p + 1) ** 2:
+                raise ValueError("each state must be a contiguous CUDA tensor of its instance's size")
+        return (ctypes.c_void_p * len(qs))(*[q.data_ptr() for q in qs])
+
+    def empty_states(self):
+        return [torch.empty(c.shape, dtype=c.torch_dtype, device="cuda") for c in self.cfgs]
+
+    def step(self, qs, nsteps: int, dt_fixed: float = 0.0, t_end: float = 0.0):
+        self._check(self.lib.cpr_batch_step(self.h, self._ptrs(qs), int(nsteps), float(dt_fixed),
+                                            float(t_end)))
+        return qs
+
+    def tune(self, qs):
+        choices = (ctypes.c_int * 12)()
+        ng = ctypes.c_int()
+        self._check(self.lib.cpr_batch_tune(self.h, self._ptrs(qs), choices, ctypes.byref(ng)))
+        return [tuple(choices[3 * k:3 * k + 3]) for k in range(ng.value)]
+
+    def get_time(self, i: int):
+        t = ctypes.c_double()
+        s = ctypes.c_longlong()
+        self._check(self.lib.cpr_batch_get_time(self.h, int(i), ctypes.byref(t), ctypes.byref(s)))
+        return t.value, s.value
+
+    def set_time(self, t: float, steps: int = 0):
+        self._check(self.lib.cpr_batch_set_time(self.h, float(t), int(steps)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cpr_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

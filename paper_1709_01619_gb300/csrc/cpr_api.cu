@@ -15,6 +15,7 @@
 #include <string>
 
 #include "../../include/cpr.h"
+#include "cpr_internal.h"
 #include "cpr_aux.cuh"
 #include "cpr_launch.h"
 
@@ -42,6 +43,8 @@ struct cpr_ctx {
     int norm_blocks = 1;
     void* host_state = nullptr;    // device copy for cpr_step_host
     void* lo = nullptr;            // low part of the state (FP32 increment form)
+    void* adj1 = nullptr;          // adjoint scratch (allocated on first use)
+    void* adj2 = nullptr;
     bool use_inc = false;          // FP32 without limiter: increment form of SSP-RK3
     const void* graph_q = nullptr;
     cudaGraphExec_t g1 = nullptr, g2 = nullptr, gK = nullptr;
@@ -138,7 +141,32 @@ static cudaError_t norms(cpr_ctx* c, const void* q, const void* ref, cudaStream_
 // ---------------------------------------------------------------------------
 // configuration
 // ---------------------------------------------------------------------------
-static const char* validate(const cpr_config* c)
+bool cpr_fill_launch_cfg(const cpr_config* cfg, LaunchCfg* out)
+{
+    LaunchCfg lc{};
+    lc.eqn = cfg->eqn;
+    lc.p = cfg->p;
+    lc.div = cfg->div;
+    lc.flux = cfg->flux == CPR_FLUX_UPWIND ? cpr::FLUX_UPWIND : cpr::FLUX_RUSANOV;
+    lc.nx = cfg->nx;
+    lc.ny = cfg->ny;
+    lc.bcx = cfg->bc_x == CPR_BC_TRANSMISSIVE;
+    lc.bcy = cfg->bc_y == CPR_BC_TRANSMISSIVE;
+    lc.ne = (long long)cfg->nx * cfg->ny;
+    lc.npts = lc.ne * (cfg->p + 1) * (cfg->p + 1);
+    lc.hx = (cfg->x1 - cfg->x0) / cfg->nx;
+    lc.hy = (cfg->y1 - cfg->y0) / cfg->ny;
+    lc.gamma = cfg->gamma;
+    lc.ax = cfg->ax;
+    lc.ay = cfg->ay;
+    lc.tvb_M = cfg->tvb_M;
+    lc.lim_eps = cfg->lim_eps;
+    if (cpr::build_tables(cfg->p, cfg->pts, &lc.tab) != 0) return false;
+    *out = lc;
+    return true;
+}
+
+const char* cpr_validate_config(const cpr_config* c)
 {
     if (!c) return "cfg is NULL";
     if (c->eqn != CPR_ADVECTION && c->eqn != CPR_EULER) return "eqn must be CPR_ADVECTION or CPR_EULER";
@@ -172,6 +200,8 @@ static void free_all(cpr_ctx* c)
     if (c->g2) cudaGraphExecDestroy(c->g2);
     if (c->gK) cudaGraphExecDestroy(c->gK);
     cudaFree(c->lo);
+    cudaFree(c->adj1);
+    cudaFree(c->adj2);
     cudaFree(c->q1);
     cudaFree(c->q2);
     cudaFree(c->avg);
@@ -192,7 +222,7 @@ extern "C" cpr_status cpr_init(const cpr_config* cfg, void* stream, cpr_ctx** ou
         return CPR_EINVAL;
     }
     *out = nullptr;
-    if (const char* msg = validate(cfg)) {
+    if (const char* msg = cpr_validate_config(cfg)) {
         g_init_err = msg;
         return CPR_EINVAL;
     }
@@ -215,29 +245,12 @@ extern "C" cpr_status cpr_init(const cpr_config* cfg, void* stream, cpr_ctx** ou
     c->nstate = c->npts * c->V;
     c->esize = cfg->dtype == CPR_F32 ? 4 : 8;
 
-    LaunchCfg& lc = c->lc;
-    lc.eqn = cfg->eqn;
-    lc.p = cfg->p;
-    lc.div = cfg->div;
-    lc.flux = cfg->flux == CPR_FLUX_UPWIND ? cpr::FLUX_UPWIND : cpr::FLUX_RUSANOV;
-    lc.nx = cfg->nx;
-    lc.ny = cfg->ny;
-    lc.bcx = cfg->bc_x == CPR_BC_TRANSMISSIVE;
-    lc.bcy = cfg->bc_y == CPR_BC_TRANSMISSIVE;
-    lc.ne = c->ne;
-    lc.npts = c->npts;
-    lc.hx = (cfg->x1 - cfg->x0) / cfg->nx;
-    lc.hy = (cfg->y1 - cfg->y0) / cfg->ny;
-    lc.gamma = cfg->gamma;
-    lc.ax = cfg->ax;
-    lc.ay = cfg->ay;
-    lc.tvb_M = cfg->tvb_M;
-    lc.lim_eps = cfg->lim_eps;
-    if (cpr::build_tables(cfg->p, cfg->pts, &lc.tab) != 0) {
+    if (!cpr_fill_launch_cfg(cfg, &c->lc)) {
         delete c;
         g_init_err = "table construction failed";
         return CPR_EINVAL;
     }
+    LaunchCfg& lc = c->lc;
 
     const int ctas = std::max(cpr::stage_ctas(lc), std::max(cpr::aux_ctas(lc), 1024));
     c->norm_blocks = (int)std::min<long long>(1024, std::max<long long>(1, (c->ne + 255) / 256));
@@ -511,12 +524,61 @@ extern "C" cpr_status cpr_get_time(cpr_ctx* c, double* t, long long* steps)
     return CPR_OK;
 }
 
-extern "C" cpr_status cpr_residual_vjp(cpr_ctx* c, const void*, const void*, void*)
+static cudaError_t vjp(cpr_ctx* c, const cpr::VjpPtrs& b, cudaStream_t s)
 {
-    return fail(c, CPR_ENOTIMPL, "cpr_residual_vjp is not built yet");
+    return c->cfg.dtype == CPR_F32 ? cpr::launch_vjp<float>(c->lc, b, s, false)
+                                   : cpr::launch_vjp<double>(c->lc, b, s, false);
 }
 
-extern "C" cpr_status cpr_step_vjp(cpr_ctx* c, const void*, const void*, void*, double)
+static cpr_status vjp_check(cpr_ctx* c)
 {
-    return fail(c, CPR_ENOTIMPL, "cpr_step_vjp is not built yet");
+    if (c->cfg.div != CPR_DIV_LP) return fail(c, CPR_EINVAL, "the adjoint needs the LP divergence");
+    if (c->cfg.limiter) return fail(c, CPR_EINVAL, "the adjoint covers unlimited runs only");
+    CPR_CUDA(c, c->cfg.dtype == CPR_F32 ? cpr::launch_vjp<float>(c->lc, cpr::VjpPtrs{}, c->stream, true)
+                                        : cpr::launch_vjp<double>(c->lc, cpr::VjpPtrs{}, c->stream, true));
+    return CPR_OK;
+}
+
+extern "C" cpr_status cpr_residual_vjp(cpr_ctx* c, const void* q, const void* rbar, void* qbar)
+{
+    if (!c) return CPR_EINVAL;
+    if (!q || !rbar || !qbar) return fail(c, CPR_EINVAL, "q_dev, rbar_dev and qbar_dev must be non-NULL");
+    if (qbar == q || qbar == rbar) return fail(c, CPR_EINVAL, "qbar_dev must not alias q_dev or rbar_dev");
+    if (!aligned(q) || !aligned(rbar) || !aligned(qbar)) return fail(c, CPR_EINVAL, "state arrays must be 16-byte aligned");
+    cpr_status st = vjp_check(c);
+    if (st != CPR_OK) return st;
+    cpr::VjpPtrs b{q, rbar, qbar, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0, 1.0};
+    CPR_CUDA(c, vjp(c, b, c->stream));
+    return CPR_OK;
+}
+
+// Transpose of one SSP-RK3 step from q with step dt, stages recomputed:
+//   b2 = 2/3 (qbar_out + dt J(q2)^T qbar_out)
+//   b1 = 1/4 (b2 + dt J(q1)^T b2)
+//   qbar_in = 1/3 qbar_out + 3/4 b2 + b1 + dt J(q)^T b1
+extern "C" cpr_status cpr_step_vjp(cpr_ctx* c, const void* q, const void* qbar_out, void* qbar_in, double dt)
+{
+    if (!c) return CPR_EINVAL;
+    if (!q || !qbar_out || !qbar_in) return fail(c, CPR_EINVAL, "q_dev, qbar_out_dev and qbar_in_dev must be non-NULL");
+    if (q == qbar_out || q == qbar_in) return fail(c, CPR_EINVAL, "q_dev must not alias the cotangents");
+    if (!aligned(q) || !aligned(qbar_out) || !aligned(qbar_in))
+        return fail(c, CPR_EINVAL, "state arrays must be 16-byte aligned");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, CPR_EINVAL, "dt must be finite and > 0");
+    cpr_status st = vjp_check(c);
+    if (st != CPR_OK) return st;
+    const size_t bytes = (size_t)c->nstate * c->esize;
+    if (!c->adj1) CPR_CUDA(c, cudaMalloc(&c->adj1, bytes));
+    if (!c->adj2) CPR_CUDA(c, cudaMalloc(&c->adj2, bytes));
+    // stage states q1, q2 with this dt (Shu-Osher form, context buffers)
+    ctrl_configure_kernel<<<1, 1, 0, c->stream>>>(c->ctrl, dt, 0.0, 0.0);
+    CPR_CUDA(c, cudaGetLastError());
+    CPR_CUDA(c, stage(c, cpr::MODE_SO1, q, nullptr, c->q1, nullptr, false, c->stream));
+    CPR_CUDA(c, stage(c, cpr::MODE_SO2, c->q1, q, c->q2, nullptr, false, c->stream));
+    cpr::VjpPtrs b2{c->q2, qbar_out, c->adj1, qbar_out, nullptr, nullptr, 2.0 / 3.0, 0.0, 0.0, 2.0 / 3.0 * dt};
+    CPR_CUDA(c, vjp(c, b2, c->stream));
+    cpr::VjpPtrs b1{c->q1, c->adj1, c->adj2, c->adj1, nullptr, nullptr, 0.25, 0.0, 0.0, 0.25 * dt};
+    CPR_CUDA(c, vjp(c, b1, c->stream));
+    cpr::VjpPtrs b0{q, c->adj2, qbar_in, qbar_out, c->adj1, c->adj2, 1.0 / 3.0, 0.75, 1.0, dt};
+    CPR_CUDA(c, vjp(c, b0, c->stream));
+    return CPR_OK;
 }

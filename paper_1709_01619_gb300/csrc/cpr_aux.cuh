@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(AuxShape<T, P, EQ>::EB) cpr_limit_kernel(const
                                              (unsigned long long)s_cnt);
     if (A.do_wave) {
         m = block_max<T>(m);
-        last_cta_time_update<T>(m, A.wave, A.ctrl, /*advance=*/true);
+        last_cta_time_update<T>(m, A.wave, A.ctrl, /*advance=*/true, blockIdx.x, gridDim.x);
     }
 }
 
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(256) cpr_wave_kernel(const AuxArgs<T> A)
         m = s > m ? s : m;
     }
     m = block_max<T>(m);
-    last_cta_time_update<T>(m, A.wave, A.ctrl, /*advance=*/false);
+    last_cta_time_update<T>(m, A.wave, A.ctrl, /*advance=*/false, blockIdx.x, gridDim.x);
 }
 
 // FP64 norms, pass 1: each CTA reduces a contiguous element range in a fixed

@@ -5,29 +5,10 @@
 
 #include "cpr_aux.cuh"
 #include "cpr_launch.h"
+#include "cpr_tabconv.cuh"
 
 namespace cpr {
 
-template <class T>
-static Tab<T> host_to_tab(const HostTab& h)
-{
-    Tab<T> t;
-    for (int a = 0; a < kMaxN; ++a) {
-        for (int l = 0; l < kMaxN; ++l) {
-            const bool in = a < h.n && l < h.n;
-            t.D[a][l] = in ? T(h.D[a][l]) : T(0);
-            t.cavg[a][l] = in ? T(h.w[a] * h.w[l] * 0.25) : T(0);
-        }
-        const bool in = a < h.n;
-        t.lm[a] = in ? T(h.lm[a]) : T(0);
-        t.lp[a] = in ? T(h.lp[a]) : T(0);
-        t.dgl[a] = in ? T(h.dgl[a]) : T(0);
-        t.dgr[a] = in ? T(h.dgr[a]) : T(0);
-        t.w[a] = in ? T(h.w[a]) : T(0);
-        t.xi[a] = in ? T(h.xi[a]) : T(0);
-    }
-    return t;
-}
 
 template <class T>
 static AuxArgs<T> make_aux(const LaunchCfg& c)
@@ -56,8 +37,8 @@ static AuxArgs<T> make_aux(const LaunchCfg& c)
     A.ph.gamma = T(c.gamma);
     A.ph.ax = T(c.ax);
     A.ph.ay = T(c.ay);
-    A.tab = host_to_tab<T>(c.tab);
-    A.tab64 = host_to_tab<double>(c.tab);
+    A.tab = host_tab<T>(c.tab);
+    A.tab64 = host_tab<double>(c.tab);
     A.gamma64 = c.gamma;
     A.ax64 = c.ax;
     A.ay64 = c.ay;
@@ -99,6 +80,18 @@ cudaError_t launch_stage(const LaunchCfg& c, int mode, const void* qs, const voi
 {
     StagePtrs b{qs, nullptr, qn, out, nullptr, avg};
     return launch_stage<T>(c, mode, b, do_wave, s);
+}
+
+template <class T>
+cudaError_t launch_vjp(const LaunchCfg& c, const VjpPtrs& b, cudaStream_t s, bool prep)
+{
+    switch (c.p) {
+    case 1: return launch_vjp_p<T, 1>(c, b, s, prep);
+    case 2: return launch_vjp_p<T, 2>(c, b, s, prep);
+    case 3: return launch_vjp_p<T, 3>(c, b, s, prep);
+    case 4: return launch_vjp_p<T, 4>(c, b, s, prep);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 template <class T>
@@ -185,6 +178,7 @@ cudaError_t launch_norms(const LaunchCfg& c, const void* q, const void* ref, int
                                               bool, cudaStream_t);                                          \
     template cudaError_t cpr::launch_stage<T>(const LaunchCfg&, int, const StagePtrs&, bool, cudaStream_t);  \
     template cudaError_t cpr::prepare_stage<T>(const LaunchCfg&);                                            \
+    template cudaError_t cpr::launch_vjp<T>(const LaunchCfg&, const VjpPtrs&, cudaStream_t, bool);          \
     template cudaError_t cpr::launch_averages<T>(const LaunchCfg&, const void*, void*, cudaStream_t);        \
     template cudaError_t cpr::launch_limit<T>(const LaunchCfg&, void*, const void*, int, cudaStream_t);      \
     template cudaError_t cpr::launch_wave<T>(const LaunchCfg&, const void*, cudaStream_t);                   \

@@ -1,0 +1,581 @@
+// cpr_batch_api.cu -- C ABI of the batched solver (include/cpr.h, cpr_batch_*).
+//
+// A batch owns, per instance, two stage buffers, the low part of the state
+// (FP32), the per-tile partial maxima and a time-control block; per order
+// group, the device work-list tables of both tile families; and the CUDA
+// graphs of the RK loop (one persistent launch per order group and stage).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "cpr_batch.cuh"
+#include "cpr_tabconv.cuh"
+#include "cpr_internal.h"
+#include "cpr_reduce.cuh"
+
+using cpr::BatchArgs;
+using cpr::BatchInst;
+using cpr::Ctrl;
+using cpr::LaunchCfg;
+
+namespace {
+
+const int kBatchStepsPerGraph = 8;
+
+struct Group {
+    int p = 0;
+    std::vector<int> members;                // instance indices
+    int total[cpr::kBatchFamilies] = {0, 0};  // work items per family
+    void* d_inst[cpr::kBatchFamilies] = {nullptr, nullptr};
+    void* h_inst[cpr::kBatchFamilies] = {nullptr, nullptr};  // pinned mirrors
+    int fam = 0;                              // chosen tile family
+    int grid = 0;                             // chosen persistent grid
+    int occ[cpr::kBatchFamilies] = {0, 0};    // resident CTAs per SM
+};
+
+thread_local std::string g_batch_init_err;
+
+}  // namespace
+
+struct cpr_batch {
+    int n = 0;
+    int V = 1;
+    int dtype = CPR_F32;
+    bool use_inc = false;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;
+    int sms = 1;
+    std::vector<cpr_config> cfgs;
+    std::vector<LaunchCfg> lcs;
+    std::vector<long long> nstate;
+    std::vector<void*> Y, Z, lo, wave;
+    Ctrl* ctrls = nullptr;
+    Ctrl* h_ctrls = nullptr;      // pinned
+    Ctrl* ctrl_backup = nullptr;  // device, for the autotuner
+    std::vector<Group> groups;
+    std::vector<const void*> x_cached;
+    cudaGraphExec_t g1 = nullptr, g2 = nullptr, gK = nullptr;
+    bool graphs_valid = false;
+    std::string err;
+};
+
+#define BATCH_CUDA(b, call)                                                                  \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            (b)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                   \
+            return CPR_ECUDA;                                                                \
+        }                                                                                    \
+    } while (0)
+
+namespace {
+
+__global__ void batch_configure_kernel(Ctrl* c, int n, double dt_fixed, double t_end, const double* cfl_h)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Ctrl* k = c + i;
+    k->dt_fixed = dt_fixed;
+    k->t_end = t_end;
+    k->cfl_h = cfl_h[i];
+    k->done = 0;
+    k->counter = 0;
+    k->parity = 0;
+    if (dt_fixed > 0.0) cpr::ctrl_next_dt(k, k->max_wave);
+}
+
+// Increment form: instances whose state ended in Y after an odd number of
+// steps are copied back to the caller's array.
+template <class T>
+__global__ void batch_parity_copy_kernel(const BatchInst<T>* inst, int V)
+{
+    const BatchInst<T>& I = inst[blockIdx.y];
+    if (!I.ctrl->parity) return;
+    const long long n = I.npts * V;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        I.X[i] = I.Y[i];
+}
+
+template <class T>
+cudaError_t batch_launch(cpr_batch* b, Group& g, int fam, int grid, int mode, int swap, cudaStream_t s)
+{
+    BatchArgs<T> B;
+    B.inst = static_cast<const BatchInst<T>*>(g.d_inst[fam]);
+    B.ninst = (int)g.members.size();
+    B.total = g.total[fam];
+    B.mode = mode;
+    B.swap = swap;
+    B.tab = cpr::host_tab<T>(b->lcs[g.members[0]].tab);
+    const LaunchCfg& lc = b->lcs[g.members[0]];
+    return fam == 0 ? cpr::batch_fam<T, 0>(g.p, lc.eqn, lc.flux, B, grid, s, 0, nullptr)
+                    : cpr::batch_fam<T, 1>(g.p, lc.eqn, lc.flux, B, grid, s, 0, nullptr);
+}
+
+cudaError_t batch_stage(cpr_batch* b, int mode, int swap, cudaStream_t s)
+{
+    for (Group& g : b->groups) {
+        cudaError_t e = b->dtype == CPR_F32 ? batch_launch<float>(b, g, g.fam, g.grid, mode, swap, s)
+                                            : batch_launch<double>(b, g, g.fam, g.grid, mode, swap, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// One RK3 step of every instance: increment form (FP32, high part in X when
+// swap == 0, else in Y) or Shu-Osher stages (FP64).
+cudaError_t batch_enqueue_step(cpr_batch* b, int swap, cudaStream_t s)
+{
+    cudaError_t e;
+    if (b->use_inc) {
+        if ((e = batch_stage(b, cpr::MODE_INC1, swap, s)) != cudaSuccess) return e;
+        if ((e = batch_stage(b, cpr::MODE_INC2, swap, s)) != cudaSuccess) return e;
+        return batch_stage(b, cpr::MODE_INC3, swap, s);
+    }
+    if ((e = batch_stage(b, cpr::MODE_SO1, 0, s)) != cudaSuccess) return e;
+    if ((e = batch_stage(b, cpr::MODE_SO2, 0, s)) != cudaSuccess) return e;
+    return batch_stage(b, cpr::MODE_SO3, 0, s);
+}
+
+cudaError_t batch_capture(cpr_batch* b, int steps, cudaGraphExec_t* exec)
+{
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t ee = cudaSuccess;
+    for (int k = 0; k < steps && ee == cudaSuccess; ++k) ee = batch_enqueue_step(b, k % 2, b->cap);
+    e = cudaStreamEndCapture(b->cap, &g);
+    if (ee != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return ee;
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
+void drop_graphs(cpr_batch* b)
+{
+    if (b->g1) cudaGraphExecDestroy(b->g1);
+    if (b->g2) cudaGraphExecDestroy(b->g2);
+    if (b->gK) cudaGraphExecDestroy(b->gK);
+    b->g1 = b->g2 = b->gK = nullptr;
+    b->graphs_valid = false;
+}
+
+cudaError_t ensure_batch_graphs(cpr_batch* b)
+{
+    if (b->graphs_valid) return cudaSuccess;
+    drop_graphs(b);
+    cudaError_t e = batch_capture(b, 1, &b->g1);
+    if (e == cudaSuccess) e = batch_capture(b, 2, &b->g2);
+    if (e == cudaSuccess) e = batch_capture(b, kBatchStepsPerGraph, &b->gK);
+    b->graphs_valid = e == cudaSuccess;
+    return e;
+}
+
+// Work-list tables of one dtype (host mirrors in pinned memory, device copy).
+template <class T>
+void fill_tables(cpr_batch* b, Group& g, const void* const* x)
+{
+    for (int fam = 0; fam < cpr::kBatchFamilies; ++fam) {
+        int tx, ty;
+        cpr::batch_tile(fam, &tx, &ty);
+        BatchInst<T>* h = static_cast<BatchInst<T>*>(g.h_inst[fam]);
+        int tile0 = 0;
+        for (size_t m = 0; m < g.members.size(); ++m) {
+            const int i = g.members[m];
+            const LaunchCfg& lc = b->lcs[i];
+            BatchInst<T>& I = h[m];
+            I.X = static_cast<T*>(const_cast<void*>(x ? x[i] : nullptr));
+            I.Y = static_cast<T*>(b->Y[i]);
+            I.Z = static_cast<T*>(b->Z[i]);
+            I.lo = static_cast<T*>(b->lo[i]);
+            I.wave = static_cast<T*>(b->wave[i]);
+            I.ctrl = b->ctrls + i;
+            I.npts = lc.npts;
+            I.nx = lc.nx;
+            I.ny = lc.ny;
+            I.bcx = lc.bcx;
+            I.bcy = lc.bcy;
+            I.tiles_x = (lc.nx + tx - 1) / tx;
+            I.ntiles = I.tiles_x * ((lc.ny + ty - 1) / ty);
+            I.tile0 = tile0;
+            tile0 += I.ntiles;
+            I.rhx2 = T(2.0 / lc.hx);
+            I.rhy2 = T(2.0 / lc.hy);
+            I.ph.gamma = T(lc.gamma);
+            I.ph.ax = T(lc.ax);
+            I.ph.ay = T(lc.ay);
+        }
+        g.total[fam] = tile0;
+    }
+}
+
+template <class T>
+cudaError_t upload_tables(cpr_batch* b, Group& g, cudaStream_t s)
+{
+    for (int fam = 0; fam < cpr::kBatchFamilies; ++fam) {
+        cudaError_t e = cudaMemcpyAsync(g.d_inst[fam], g.h_inst[fam], sizeof(BatchInst<T>) * g.members.size(),
+                                        cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <class T>
+cudaError_t group_occupancy(cpr_batch* b, Group& g)
+{
+    const LaunchCfg& lc = b->lcs[g.members[0]];
+    BatchArgs<T> B{};
+    for (int fam = 0; fam < cpr::kBatchFamilies; ++fam) {
+        cudaError_t e = fam == 0 ? cpr::batch_fam<T, 0>(g.p, lc.eqn, lc.flux, B, 0, 0, 1, nullptr)
+                                 : cpr::batch_fam<T, 1>(g.p, lc.eqn, lc.flux, B, 0, 0, 1, nullptr);
+        if (e != cudaSuccess) return e;
+        e = fam == 0 ? cpr::batch_fam<T, 0>(g.p, lc.eqn, lc.flux, B, 0, 0, 2, &g.occ[0])
+                     : cpr::batch_fam<T, 1>(g.p, lc.eqn, lc.flux, B, 0, 0, 2, &g.occ[1]);
+        if (e != cudaSuccess) return e;
+        g.occ[fam] = std::max(1, g.occ[fam]);
+    }
+    g.fam = 0;
+    g.grid = std::min(g.total[0], b->sms * g.occ[0]);
+    return cudaSuccess;
+}
+
+void free_batch(cpr_batch* b)
+{
+    drop_graphs(b);
+    for (void* p : b->Y) cudaFree(p);
+    for (void* p : b->Z) cudaFree(p);
+    for (void* p : b->lo) cudaFree(p);
+    for (void* p : b->wave) cudaFree(p);
+    for (Group& g : b->groups)
+        for (int f = 0; f < cpr::kBatchFamilies; ++f) {
+            cudaFree(g.d_inst[f]);
+            if (g.h_inst[f]) cudaFreeHost(g.h_inst[f]);
+        }
+    cudaFree(b->ctrls);
+    cudaFree(b->ctrl_backup);
+    if (b->h_ctrls) cudaFreeHost(b->h_ctrls);
+    if (b->cap) cudaStreamDestroy(b->cap);
+}
+
+}  // namespace
+
+extern "C" cpr_status cpr_batch_init(const cpr_config* cfgs, int n, void* stream, cpr_batch** out)
+{
+    if (!out) {
+        g_batch_init_err = "out is NULL";
+        return CPR_EINVAL;
+    }
+    *out = nullptr;
+    if (!cfgs || n < 1) {
+        g_batch_init_err = "cfgs must hold n >= 1 configurations";
+        return CPR_EINVAL;
+    }
+    for (int i = 0; i < n; ++i) {
+        if (const char* msg = cpr_validate_config(&cfgs[i])) {
+            g_batch_init_err = std::string("instance ") + std::to_string(i) + ": " + msg;
+            return CPR_EINVAL;
+        }
+        const cpr_config& a = cfgs[0];
+        const cpr_config& c = cfgs[i];
+        if (c.eqn != a.eqn || c.dtype != a.dtype || c.flux != a.flux) {
+            g_batch_init_err = "all instances need the same eqn, dtype and flux";
+            return CPR_EINVAL;
+        }
+        if (c.div != CPR_DIV_LP || c.pts != CPR_PTS_GAUSS || c.limiter || c.flux == CPR_FLUX_ROE) {
+            g_batch_init_err = "batches run Gauss points, LP divergence, no limiter, Rusanov or upwind flux";
+            return CPR_EINVAL;
+        }
+    }
+    cpr_batch* b = new (std::nothrow) cpr_batch();
+    if (!b) {
+        g_batch_init_err = "host allocation failed";
+        return CPR_ENOMEM;
+    }
+    b->n = n;
+    b->V = cfgs[0].eqn == CPR_EULER ? 4 : 1;
+    b->dtype = cfgs[0].dtype;
+    b->use_inc = b->dtype == CPR_F32;
+    b->stream = static_cast<cudaStream_t>(stream);
+    b->cfgs.assign(cfgs, cfgs + n);
+    b->lcs.resize(n);
+    b->nstate.resize(n);
+    b->Y.assign(n, nullptr);
+    b->Z.assign(n, nullptr);
+    b->lo.assign(n, nullptr);
+    b->wave.assign(n, nullptr);
+    const size_t esize = b->dtype == CPR_F32 ? 4 : 8;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        if (!cpr_fill_launch_cfg(&cfgs[i], &b->lcs[i])) {
+            free_batch(b);
+            delete b;
+            g_batch_init_err = "table construction failed";
+            return CPR_EINVAL;
+        }
+        LaunchCfg& lc = b->lcs[i];
+        b->nstate[i] = lc.npts * b->V;
+        const size_t bytes = (size_t)b->nstate[i] * esize;
+        int tiles = 0;
+        for (int fam = 0; fam < cpr::kBatchFamilies; ++fam) {
+            int tx, ty;
+            cpr::batch_tile(fam, &tx, &ty);
+            tiles = std::max(tiles, ((lc.nx + tx - 1) / tx) * ((lc.ny + ty - 1) / ty));
+        }
+        tiles = std::max(tiles, 1024);  // also the CFL start pass
+        e = cudaMalloc(&b->Y[i], bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&b->Z[i], bytes);
+        if (e == cudaSuccess && b->use_inc) e = cudaMalloc(&b->lo[i], bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&b->wave[i], (size_t)tiles * esize);
+    }
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->ctrls, sizeof(Ctrl) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->ctrl_backup, sizeof(Ctrl) * n);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_ctrls, sizeof(Ctrl) * n);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->ctrls, 0, sizeof(Ctrl) * n, b->stream);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        b->lcs[i].ctrl = b->ctrls + i;
+        b->lcs[i].wave = b->wave[i];
+    }
+    // order groups
+    for (int p = 1; p <= 4 && e == cudaSuccess; ++p) {
+        Group g;
+        g.p = p;
+        for (int i = 0; i < n; ++i)
+            if (cfgs[i].p == p) g.members.push_back(i);
+        if (g.members.empty()) continue;
+        const size_t isz = (b->dtype == CPR_F32 ? sizeof(BatchInst<float>) : sizeof(BatchInst<double>)) *
+                           g.members.size();
+        for (int fam = 0; fam < cpr::kBatchFamilies && e == cudaSuccess; ++fam) {
+            e = cudaMalloc(&g.d_inst[fam], isz);
+            if (e == cudaSuccess) e = cudaMallocHost(&g.h_inst[fam], isz);
+        }
+        if (e != cudaSuccess) break;
+        if (b->dtype == CPR_F32) {
+            fill_tables<float>(b, g, nullptr);
+            e = group_occupancy<float>(b, g);
+        } else {
+            fill_tables<double>(b, g, nullptr);
+            e = group_occupancy<double>(b, g);
+        }
+        b->groups.push_back(g);
+    }
+    if (e != cudaSuccess) {
+        g_batch_init_err = std::string("CUDA: ") + cudaGetErrorString(e);
+        const cpr_status st = e == cudaErrorMemoryAllocation ? CPR_ENOMEM : CPR_ECUDA;
+        free_batch(b);
+        delete b;
+        return st;
+    }
+    b->x_cached.assign(n, nullptr);
+    *out = b;
+    return CPR_OK;
+}
+
+extern "C" void cpr_batch_destroy(cpr_batch* b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    free_batch(b);
+    delete b;
+}
+
+extern "C" const char* cpr_batch_last_error(const cpr_batch* b)
+{
+    return b ? b->err.c_str() : g_batch_init_err.c_str();
+}
+
+static cpr_status batch_bind(cpr_batch* b, void* const* q)
+{
+    if (!q) {
+        b->err = "q_devs must be non-NULL";
+        return CPR_EINVAL;
+    }
+    bool changed = false;
+    for (int i = 0; i < b->n; ++i) {
+        if (!q[i] || (reinterpret_cast<uintptr_t>(q[i]) & 15u)) {
+            b->err = "every q_devs[i] must be a non-NULL 16-byte aligned device array";
+            return CPR_EINVAL;
+        }
+        changed = changed || q[i] != b->x_cached[i];
+    }
+    if (!changed) return CPR_OK;
+    // the device tables are read by graphs in flight: wait before rewriting
+    BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+    for (Group& g : b->groups) {
+        if (b->dtype == CPR_F32) {
+            fill_tables<float>(b, g, q);
+            BATCH_CUDA(b, upload_tables<float>(b, g, b->stream));
+        } else {
+            fill_tables<double>(b, g, q);
+            BATCH_CUDA(b, upload_tables<double>(b, g, b->stream));
+        }
+    }
+    for (int i = 0; i < b->n; ++i) b->x_cached[i] = q[i];
+    return CPR_OK;
+}
+
+static cpr_status batch_prelude(cpr_batch* b, void* const* q, double dt_fixed, double t_end, double* cfl_h_dev)
+{
+    batch_configure_kernel<<<(b->n + 127) / 128, 128, 0, b->stream>>>(b->ctrls, b->n, dt_fixed, t_end, cfl_h_dev);
+    BATCH_CUDA(b, cudaGetLastError());
+    if (dt_fixed <= 0.0)
+        for (int i = 0; i < b->n; ++i)
+            BATCH_CUDA(b, b->dtype == CPR_F32 ? cpr::launch_wave<float>(b->lcs[i], q[i], b->stream)
+                                              : cpr::launch_wave<double>(b->lcs[i], q[i], b->stream));
+    if (b->use_inc)
+        for (int i = 0; i < b->n; ++i)
+            BATCH_CUDA(b, cudaMemsetAsync(b->lo[i], 0, (size_t)b->nstate[i] * 4, b->stream));
+    return CPR_OK;
+}
+
+extern "C" cpr_status cpr_batch_step(cpr_batch* b, void* const* q, int nsteps, double dt_fixed, double t_end)
+{
+    if (!b) return CPR_EINVAL;
+    if (nsteps < 0 || !std::isfinite(dt_fixed) || !std::isfinite(t_end)) {
+        b->err = "nsteps must be >= 0, dt_fixed and t_end finite";
+        return CPR_EINVAL;
+    }
+    if (dt_fixed <= 0.0)
+        for (const cpr_config& c : b->cfgs)
+            if (!(c.cfl > 0.0)) {
+                b->err = "CFL steps need cfg.cfl > 0 for every instance";
+                return CPR_EINVAL;
+            }
+    cpr_status st = batch_bind(b, q);
+    if (st != CPR_OK || nsteps == 0) return st;
+    // per-instance cfl * h, staged through the pinned control mirror
+    double* cflh = reinterpret_cast<double*>(b->h_ctrls);
+    static_assert(sizeof(Ctrl) >= sizeof(double), "control block too small");
+    BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < b->n; ++i) cflh[i] = b->cfgs[i].cfl * std::min(b->lcs[i].hx, b->lcs[i].hy);
+    double* cflh_dev = reinterpret_cast<double*>(b->ctrl_backup);
+    BATCH_CUDA(b, cudaMemcpyAsync(cflh_dev, cflh, sizeof(double) * b->n, cudaMemcpyHostToDevice, b->stream));
+    if ((st = batch_prelude(b, q, dt_fixed, t_end, cflh_dev)) != CPR_OK) return st;
+    BATCH_CUDA(b, ensure_batch_graphs(b));
+    for (int k = 0; k < nsteps / kBatchStepsPerGraph; ++k) BATCH_CUDA(b, cudaGraphLaunch(b->gK, b->stream));
+    const int rest = nsteps % kBatchStepsPerGraph;
+    if (b->use_inc) {
+        for (int k = 0; k < rest / 2; ++k) BATCH_CUDA(b, cudaGraphLaunch(b->g2, b->stream));
+        if (rest % 2) BATCH_CUDA(b, cudaGraphLaunch(b->g1, b->stream));
+        for (Group& g : b->groups) {
+            batch_parity_copy_kernel<float><<<dim3(64, (unsigned)g.members.size()), 256, 0, b->stream>>>(
+                static_cast<const BatchInst<float>*>(g.d_inst[0]), b->V);
+            BATCH_CUDA(b, cudaGetLastError());
+        }
+    } else {
+        for (int k = 0; k < rest; ++k) BATCH_CUDA(b, cudaGraphLaunch(b->g1, b->stream));
+    }
+    return CPR_OK;
+}
+
+extern "C" cpr_status cpr_batch_get_time(cpr_batch* b, int i, double* t, long long* steps)
+{
+    if (!b) return CPR_EINVAL;
+    if (i < 0 || i >= b->n) {
+        b->err = "instance index out of range";
+        return CPR_EINVAL;
+    }
+    BATCH_CUDA(b, cudaMemcpyAsync(b->h_ctrls + i, b->ctrls + i, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream));
+    BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+    if (t) *t = b->h_ctrls[i].t;
+    if (steps) *steps = b->h_ctrls[i].steps;
+    return CPR_OK;
+}
+
+extern "C" cpr_status cpr_batch_set_time(cpr_batch* b, double t, long long steps)
+{
+    if (!b) return CPR_EINVAL;
+    if (!std::isfinite(t) || steps < 0) {
+        b->err = "t must be finite and steps >= 0";
+        return CPR_EINVAL;
+    }
+    BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+    BATCH_CUDA(b, cudaMemcpy(b->h_ctrls, b->ctrls, sizeof(Ctrl) * b->n, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < b->n; ++i) {
+        b->h_ctrls[i].t = t;
+        b->h_ctrls[i].steps = steps;
+        b->h_ctrls[i].done = 0;
+        b->h_ctrls[i].last = 0;
+    }
+    BATCH_CUDA(b, cudaMemcpy(b->ctrls, b->h_ctrls, sizeof(Ctrl) * b->n, cudaMemcpyHostToDevice));
+    return CPR_OK;
+}
+
+// Autotuner: for every order group, time one RK3 step of that group (the
+// stages that leave the caller's arrays untouched) for every tile family and
+// every persistent-grid size of 1..occupancy CTAs per SM, and keep the
+// fastest.  The time-control blocks are saved and restored around the runs.
+extern "C" cpr_status cpr_batch_tune(cpr_batch* b, void* const* q, int* choices, int* ngroups)
+{
+    if (!b) return CPR_EINVAL;
+    cpr_status st = batch_bind(b, q);
+    if (st != CPR_OK) return st;
+    BATCH_CUDA(b, cudaMemcpyAsync(b->ctrl_backup, b->ctrls, sizeof(Ctrl) * b->n, cudaMemcpyDeviceToDevice,
+                                  b->stream));
+    // a small fixed step, no end time, for the timing runs
+    batch_configure_kernel<<<(b->n + 127) / 128, 128, 0, b->stream>>>(b->ctrls, b->n, 1e-6, 0.0,
+                                                                       reinterpret_cast<double*>(b->ctrl_backup));
+    BATCH_CUDA(b, cudaGetLastError());
+    cudaEvent_t e0, e1;
+    BATCH_CUDA(b, cudaEventCreate(&e0));
+    BATCH_CUDA(b, cudaEventCreate(&e1));
+    const int modes_inc[3] = {cpr::MODE_INC1, cpr::MODE_INC2, cpr::MODE_INC3};
+    const int modes_so[2] = {cpr::MODE_SO1, cpr::MODE_SO2};  // SO3 writes the state
+    for (Group& g : b->groups) {
+        float best = 1e30f;
+        int best_fam = g.fam, best_grid = g.grid;
+        for (int fam = 0; fam < cpr::kBatchFamilies; ++fam)
+            for (int c = 1; c <= g.occ[fam]; ++c) {
+                const int grid = std::min(g.total[fam], b->sms * c);
+                auto run = [&]() -> cudaError_t {
+                    const int nm = b->use_inc ? 3 : 2;
+                    for (int m = 0; m < nm; ++m) {
+                        const int mode = b->use_inc ? modes_inc[m] : modes_so[m];
+                        cudaError_t e = b->dtype == CPR_F32 ? batch_launch<float>(b, g, fam, grid, mode, 0, b->stream)
+                                                            : batch_launch<double>(b, g, fam, grid, mode, 0, b->stream);
+                        if (e != cudaSuccess) return e;
+                    }
+                    return cudaSuccess;
+                };
+                BATCH_CUDA(b, run());
+                BATCH_CUDA(b, cudaEventRecord(e0, b->stream));
+                for (int r = 0; r < 3; ++r) BATCH_CUDA(b, run());
+                BATCH_CUDA(b, cudaEventRecord(e1, b->stream));
+                BATCH_CUDA(b, cudaEventSynchronize(e1));
+                float ms = 0.f;
+                BATCH_CUDA(b, cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) {
+                    best = ms;
+                    best_fam = fam;
+                    best_grid = grid;
+                }
+            }
+        g.fam = best_fam;
+        g.grid = best_grid;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    BATCH_CUDA(b, cudaMemcpyAsync(b->ctrls, b->ctrl_backup, sizeof(Ctrl) * b->n, cudaMemcpyDeviceToDevice,
+                                  b->stream));
+    BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+    drop_graphs(b);
+    if (ngroups) *ngroups = (int)b->groups.size();
+    if (choices)
+        for (size_t k = 0; k < b->groups.size(); ++k) {
+            choices[3 * k] = b->groups[k].p;
+            choices[3 * k + 1] = b->groups[k].fam;
+            choices[3 * k + 2] = b->groups[k].grid;
+        }
+    return CPR_OK;
+}

@@ -1,0 +1,5 @@
+// Batched stage kernel instantiation: float, tile family 0.
+#include "cpr_batch_inst.cuh"
+namespace cpr {
+CPR_INSTANTIATE_BATCH(float, 0)
+}

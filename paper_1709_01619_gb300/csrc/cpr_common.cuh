@@ -308,6 +308,105 @@ __device__ __forceinline__ void common_flux_delta(const Ref<T>& r, const T* dm, 
     }
 }
 
+// ---- transposed linearisations (discrete adjoint) --------------------------
+
+// qbar += (dF_DIR/dq)^T w at state q (F_DIR the x- or y-flux of Eq. 4).
+template <int EQ, int DIR, class T>
+__device__ __forceinline__ void flux_vjp(const T* q, const T* w, const Phys<T>& ph, T* qbar)
+{
+    if constexpr (EQ == EQ_ADV) {
+        qbar[0] += (DIR == 0 ? ph.ax : ph.ay) * w[0];
+    } else {
+        const T g1 = ph.gamma - T(1);
+        const T r = q[0], ir = T(1) / r;
+        const T u = q[1] * ir, v = q[2] * ir;
+        const T p = g1 * (q[3] - T(0.5) * (q[1] * u + q[2] * v));
+        const T vn = DIR == 0 ? u : v;
+        const T nx = DIR == 0 ? T(1) : T(0), ny = DIR == 0 ? T(0) : T(1);
+        const T dvn[4] = {-vn * ir, nx * ir, ny * ir, T(0)};
+        const T dpq[4] = {g1 * T(0.5) * (u * u + v * v), -g1 * u, -g1 * v, g1};
+        const T C = w[1] * q[1] + w[2] * q[2] + w[3] * (q[3] + p);
+        const T Pc = w[1] * nx + w[2] * ny + w[3] * vn;
+        qbar[0] += C * dvn[0] + Pc * dpq[0];
+        qbar[1] += w[0] * nx + vn * w[1] + C * dvn[1] + Pc * dpq[1];
+        qbar[2] += w[0] * ny + vn * w[2] + C * dvn[2] + Pc * dpq[2];
+        qbar[3] += vn * w[3] + Pc * dpq[3];
+    }
+}
+
+// Gradient of the signal speed |Vn| + c (Euler).
+template <int DIR, class T>
+__device__ __forceinline__ void speed_grad(const T* q, const Phys<T>& ph, T* gs)
+{
+    const T g1 = ph.gamma - T(1);
+    const T r = q[0], ir = T(1) / r;
+    const T u = q[1] * ir, v = q[2] * ir;
+    const T p = g1 * (q[3] - T(0.5) * (q[1] * u + q[2] * v));
+    const T cs = dsqrt(ph.gamma * p * ir);
+    const T vn = DIR == 0 ? u : v;
+    const T sg = vn >= T(0) ? T(1) : T(-1);
+    const T nx = DIR == 0 ? T(1) : T(0), ny = DIR == 0 ? T(0) : T(1);
+    const T dvn[4] = {-vn * ir, nx * ir, ny * ir, T(0)};
+    const T dpq[4] = {g1 * T(0.5) * (u * u + v * v), -g1 * u, -g1 * v, g1};
+    const T k = ph.gamma / (T(2) * cs * r);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) gs[m] = sg * dvn[m] + k * (dpq[m] - (m == 0 ? p * ir : T(0)));
+}
+
+// Transpose of the common flux (Rusanov with lambda the larger one-sided
+// speed, differentiated on the branch the forward takes; or upwind):
+// qbm, qbp = cotangents of the lower and upper states for cotangent w.
+template <int EQ, int FLUX, int DIR, class T>
+__device__ __forceinline__ void common_flux_vjp(const T* qm, const T* qp, const T* w, const Phys<T>& ph, T* qbm,
+                                                T* qbp)
+{
+    if constexpr (EQ == EQ_ADV) {
+        const T an = DIR == 0 ? ph.ax : ph.ay;
+        if constexpr (FLUX == FLUX_UPWIND) {
+            qbm[0] = an >= T(0) ? an * w[0] : T(0);
+            qbp[0] = an >= T(0) ? T(0) : an * w[0];
+        } else {
+            const T lam = an >= T(0) ? an : -an;
+            qbm[0] = T(0.5) * an * w[0] + T(0.5) * lam * w[0];
+            qbp[0] = T(0.5) * an * w[0] - T(0.5) * lam * w[0];
+        }
+    } else {
+        T hw[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            hw[k] = T(0.5) * w[k];
+            qbm[k] = T(0);
+            qbp[k] = T(0);
+        }
+        flux_vjp<EQ, DIR>(qm, hw, ph, qbm);
+        flux_vjp<EQ, DIR>(qp, hw, ph, qbp);
+        T um, vm, up, vp;
+        const T pm = pressure(qm, ph.gamma, um, vm);
+        const T pp = pressure(qp, ph.gamma, up, vp);
+        const T vnm = DIR == 0 ? um : vm, vnp = DIR == 0 ? up : vp;
+        const T sm = (vnm >= T(0) ? vnm : -vnm) + dsqrt(ph.gamma * pm / qm[0]);
+        const T sp = (vnp >= T(0) ? vnp : -vnp) + dsqrt(ph.gamma * pp / qp[0]);
+        const T lam = sm >= sp ? sm : sp;
+        T jump = T(0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            qbm[k] += T(0.5) * lam * w[k];
+            qbp[k] -= T(0.5) * lam * w[k];
+            jump += w[k] * (qp[k] - qm[k]);
+        }
+        T gs[4];
+        if (sm >= sp) {
+            speed_grad<DIR>(qm, ph, gs);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) qbm[k] -= T(0.5) * jump * gs[k];
+        } else {
+            speed_grad<DIR>(qp, ph, gs);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) qbp[k] -= T(0.5) * jump * gs[k];
+        }
+    }
+}
+
 // Minmod functions of the limiter (Sec. 2.6).
 template <class T>
 __device__ __forceinline__ T minmod2(T a, T b)

@@ -92,4 +92,38 @@ cudaError_t launch_wave(const LaunchCfg& c, const void* q, cudaStream_t s);
 template <class T>
 cudaError_t launch_norms(const LaunchCfg& c, const void* q, const void* ref, int nblocks, cudaStream_t s);
 
+// ---- discrete adjoint (cpr_adjoint.cuh) -----------------------------------
+// out = c0 X0 + c1 X1 + c2 X2 + cv (dR/dq)^T(q) rbar; the X are nullable.
+struct VjpPtrs {
+    const void* q;
+    const void* rbar;
+    void* out;
+    const void* X0;
+    const void* X1;
+    const void* X2;
+    double c0, c1, c2, cv;
+};
+template <class T, int P>
+cudaError_t launch_vjp_p(const LaunchCfg& c, const VjpPtrs& b, cudaStream_t s, bool prepare);
+template <class T>
+cudaError_t launch_vjp(const LaunchCfg& c, const VjpPtrs& b, cudaStream_t s, bool prepare);
+
+// ---- batched launches (cpr_batch.cuh) ------------------------------------
+template <class T>
+struct BatchArgs;
+
+// Elements per tile of tile family fam of the batched kernels.
+inline void batch_tile(int fam, int* tx, int* ty)
+{
+    *tx = fam == 0 ? 8 : 16;
+    *ty = fam == 0 ? 8 : 4;
+}
+constexpr int kBatchFamilies = 2;
+
+// One launch of the batched stage kernel of order p.  what 0: launch;
+// 1: set the kernel's shared-memory limit; 2: *occ = resident CTAs per SM.
+template <class T, int FAM>
+cudaError_t batch_fam(int p, int eqn, int flux, const BatchArgs<T>& B, int grid, cudaStream_t s, int what,
+                      int* occ);
+
 }  // namespace cpr

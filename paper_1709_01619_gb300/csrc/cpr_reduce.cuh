@@ -69,23 +69,25 @@ __device__ __forceinline__ void ctrl_advance(Ctrl* c, double max_speed)
 }
 
 // Last-CTA reduction of the per-CTA maxima (call with the CTA maximum in m,
-// from all threads of the CTA).  advance: close the step (stage 3) or only
-// set the next step size (start of a run).
+// from all threads of the CTA).  slot: this CTA's (or tile's) entry among
+// nslots partials.  advance: close the step (stage 3) or only set the next
+// step size (start of a run).
 template <class T>
-__device__ __forceinline__ void last_cta_time_update(T m, T* partial, Ctrl* ctrl, bool advance)
+__device__ __forceinline__ void last_cta_time_update(T m, T* partial, Ctrl* ctrl, bool advance, int slot,
+                                                     int nslots)
 {
     __shared__ int s_last;
     if (threadIdx.x == 0) {
-        partial[blockIdx.x] = m;
+        partial[slot] = m;
         __threadfence();
         const unsigned int ticket = atomicAdd(&ctrl->counter, 1u);
-        s_last = ticket == gridDim.x - 1;
+        s_last = ticket == (unsigned int)nslots - 1;
     }
     __syncthreads();
     if (s_last) {
         __threadfence();
         T r = T(0);
-        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        for (int i = threadIdx.x; i < nslots; i += blockDim.x) {
             T w = __ldcg(partial + i);
             r = w > r ? w : r;
         }

@@ -216,14 +216,17 @@ constexpr int stage_min_blocks()
     return sizeof(T) == 8 ? 1 : (N <= 4 ? CPR_STAGE_MINB_FP32 : 2);
 }
 
+// One tile of the stage: the work of one CTA.  tile indexes the instance's
+// TX x TY tiles (row-major); threads tid >= NT of a wider CTA only take part
+// in the barriers.  slot / nslots: this tile's entry in the per-CTA partial
+// maxima of the instance (the last tile to finish reduces them).
 template <class T, int P, int EQ, int DIV, int FLUX, int TX, int TY, bool DELTA>
-__global__ void __launch_bounds__(TX * TY * (P + 1), (stage_min_blocks<T, P + 1>()))
-cpr_stage_kernel(const StageArgs<T> A)
+__device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& tb, int tile, int tid,
+                                           unsigned char* smem_raw, int slot, int nslots)
 {
     constexpr int N = P + 1, NN = N * N, V = NVars<EQ>::value;
     constexpr int NT = TX * TY * N;
     using L = StageLayout<N, V, TX, TY>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sq = reinterpret_cast<T*>(smem_raw);
     T* rS = sq;          // y-part of R, once the tile copy is dead
     T* xR = sq + L::SQ;
@@ -237,15 +240,14 @@ cpr_stage_kernel(const StageArgs<T> A)
 
     if (A.mode > 0 && A.ctrl->done) return;  // t_end reached: uniform exit
 
-    const int tid = threadIdx.x;
-    const int i0 = (blockIdx.x % A.tiles_x) * TX;
-    const int j0 = (blockIdx.x / A.tiles_x) * TY;
+    const bool active = tid < NT;
+    const int i0 = (tile % A.tiles_x) * TX;
+    const int j0 = (tile / A.tiles_x) * TY;
     const int TXe = min(TX, A.nx - i0), TYe = min(TY, A.ny - j0);
     const int el = tid / N, k = tid % N;
     const int tx = el % TX, ty = el / TX;
-    const bool valid = tx < TXe && ty < TYe;
+    const bool valid = active && tx < TXe && ty < TYe;
     const long long e = (long long)(j0 + ty) * A.nx + (i0 + tx);
-    const Tab<T>& tb = A.tab;
     const bool addb = A.mode == MODE_INC2 || A.mode == MODE_INC3;
 
     // ---- phase 1: tile rows, references, halo lines -----------------------
@@ -266,7 +268,7 @@ cpr_stage_kernel(const StageArgs<T> A)
     }
     {
         constexpr int NXH = 2 * TY * N, NYH = 2 * TX * N;
-        for (int t = tid; t < NXH + NYH; t += NT) {
+        for (int t = tid; active && t < NXH + NYH; t += NT) {
             const bool xdir = t < NXH;
             const int r0 = xdir ? t : t - NXH;
             const int side = xdir ? r0 / (TY * N) : r0 / (TX * N);
@@ -627,8 +629,17 @@ cpr_stage_kernel(const StageArgs<T> A)
             }
         }
         m = block_max<T>(m);
-        last_cta_time_update<T>(m, A.wave, A.ctrl, /*advance=*/true);
+        last_cta_time_update<T>(m, A.wave, A.ctrl, /*advance=*/true, slot, nslots);
     }
+}
+
+template <class T, int P, int EQ, int DIV, int FLUX, int TX, int TY, bool DELTA>
+__global__ void __launch_bounds__(TX * TY * (P + 1), (stage_min_blocks<T, P + 1>()))
+cpr_stage_kernel(const StageArgs<T> A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    stage_tile<T, P, EQ, DIV, FLUX, TX, TY, DELTA>(A, A.tab, blockIdx.x, threadIdx.x, smem_raw, blockIdx.x,
+                                                   gridDim.x);
 }
 
 }  // namespace cpr

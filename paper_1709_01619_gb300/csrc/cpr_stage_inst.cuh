@@ -4,30 +4,12 @@
 #pragma once
 
 #include "cpr_launch.h"
+#include "cpr_tabconv.cuh"
 #include "cpr_stage.cuh"
+#include "cpr_adjoint.cuh"
 
 namespace cpr {
 
-template <class T>
-inline Tab<T> to_tab(const HostTab& h)
-{
-    Tab<T> t;
-    for (int a = 0; a < kMaxN; ++a) {
-        for (int l = 0; l < kMaxN; ++l) {
-            const bool in = a < h.n && l < h.n;
-            t.D[a][l] = in ? T(h.D[a][l]) : T(0);
-            t.cavg[a][l] = in ? T(h.w[a] * h.w[l] * 0.25) : T(0);
-        }
-        const bool in = a < h.n;
-        t.lm[a] = in ? T(h.lm[a]) : T(0);
-        t.lp[a] = in ? T(h.lp[a]) : T(0);
-        t.dgl[a] = in ? T(h.dgl[a]) : T(0);
-        t.dgr[a] = in ? T(h.dgr[a]) : T(0);
-        t.w[a] = in ? T(h.w[a]) : T(0);
-        t.xi[a] = in ? T(h.xi[a]) : T(0);
-    }
-    return t;
-}
 
 template <class T, int P, int EQ, int DIV, int FLUX>
 static cudaError_t stage_one(const LaunchCfg& c, const StageArgs<T>& A, int ctas, cudaStream_t s, bool prep)
@@ -81,7 +63,7 @@ static StageArgs<T> make_stage_args(const LaunchCfg& c, int mode, const StagePtr
     A.ph.gamma = T(c.gamma);
     A.ph.ax = T(c.ax);
     A.ph.ay = T(c.ay);
-    A.tab = to_tab<T>(c.tab);
+    A.tab = host_tab<T>(c.tab);
     return A;
 }
 
@@ -100,8 +82,66 @@ cudaError_t prepare_stage_p(const LaunchCfg& c)
     return stage_dispatch<T, P>(c, A, 0, 0, true);
 }
 
+// Tile of the adjoint kernel (8 x 8, 8 x 4 where 8 x 8 would exceed the
+// shared memory of one CTA).
+template <class T, int P>
+struct VjpTile {
+    static constexpr int X = 8;
+    static constexpr int Y = (sizeof(T) == 8 && P == 4) ? 4 : 8;
+};
+
+template <class T, int P, int EQ, int FLUX>
+static cudaError_t vjp_one(const LaunchCfg& c, const VjpPtrs& b, cudaStream_t s, bool prep)
+{
+    constexpr int N = P + 1, V = NVars<EQ>::value;
+    constexpr int TX = VjpTile<T, P>::X, TY = VjpTile<T, P>::Y;
+    auto kern = cpr_residual_vjp_kernel<T, P, EQ, FLUX, TX, TY>;
+    const size_t smem = sizeof(T) * VjpLayout<N, V, TX, TY>::TOTAL;
+    if (prep) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    VjpArgs<T> A;
+    A.q = static_cast<const T*>(b.q);
+    A.rbar = static_cast<const T*>(b.rbar);
+    A.out = static_cast<T*>(b.out);
+    A.X0 = static_cast<const T*>(b.X0);
+    A.X1 = static_cast<const T*>(b.X1);
+    A.X2 = static_cast<const T*>(b.X2);
+    A.c0 = T(b.c0);
+    A.c1 = T(b.c1);
+    A.c2 = T(b.c2);
+    A.cv = T(b.cv);
+    A.npts = c.npts;
+    A.nx = c.nx;
+    A.ny = c.ny;
+    A.bcx = c.bcx;
+    A.bcy = c.bcy;
+    A.tiles_x = (c.nx + TX - 1) / TX;
+    A.rhx2 = T(2.0 / c.hx);
+    A.rhy2 = T(2.0 / c.hy);
+    A.ph.gamma = T(c.gamma);
+    A.ph.ax = T(c.ax);
+    A.ph.ay = T(c.ay);
+    A.tab = host_tab<T>(c.tab);
+    for (int a = 0; a < kMaxN; ++a)
+        for (int l = 0; l < kMaxN; ++l)
+            A.M[a][l] = (a < N && l < N)
+                            ? T(c.tab.D[a][l] - c.tab.lm[l] * c.tab.dgl[a] - c.tab.lp[l] * c.tab.dgr[a])
+                            : T(0);
+    const int ctas = A.tiles_x * ((c.ny + TY - 1) / TY);
+    kern<<<ctas, TX * TY * N, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <class T, int P>
+cudaError_t launch_vjp_p(const LaunchCfg& c, const VjpPtrs& b, cudaStream_t s, bool prep)
+{
+    if (c.eqn == EQ_EULER) return vjp_one<T, P, EQ_EULER, FLUX_RUSANOV>(c, b, s, prep);
+    if (c.flux == FLUX_UPWIND) return vjp_one<T, P, EQ_ADV, FLUX_UPWIND>(c, b, s, prep);
+    return vjp_one<T, P, EQ_ADV, FLUX_RUSANOV>(c, b, s, prep);
+}
+
 }  // namespace cpr
 
 #define CPR_INSTANTIATE_STAGE(T, P)                                                                     \
     template cudaError_t cpr::launch_stage_p<T, P>(const LaunchCfg&, int, const StagePtrs&, bool, cudaStream_t); \
-    template cudaError_t cpr::prepare_stage_p<T, P>(const LaunchCfg&);
+    template cudaError_t cpr::prepare_stage_p<T, P>(const LaunchCfg&);                                  \
+    template cudaError_t cpr::launch_vjp_p<T, P>(const LaunchCfg&, const VjpPtrs&, cudaStream_t, bool);

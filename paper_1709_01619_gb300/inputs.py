@@ -82,6 +82,15 @@ def radial_shock(x, y, radius: float = 0.4, gamma: float = GAMMA) -> np.ndarray:
     return conserved(rho, z, z, p, gamma)
 
 
+def entropy_wave(x, y, lx: float, ly: float, amp: float = 0.2, u: float = 1.0, v: float = 0.5,
+                 p: float = 1.0, gamma: float = GAMMA) -> np.ndarray:
+    """Density wave rho = 1 + amp sin(2 pi x / lx) sin(2 pi y / ly) carried by a
+    uniform flow (u, v) at uniform pressure: a smooth periodic Euler solution
+    on [0, lx] x [0, ly] that is advected unchanged."""
+    rho = 1.0 + amp * np.sin(2 * np.pi * x / lx) * np.sin(2 * np.pi * y / ly)
+    return conserved(rho, np.full_like(rho, u), np.full_like(rho, v), np.full_like(rho, p), gamma)
+
+
 def freestream(x, rho=1.0, u=0.7, v=-0.3, p=0.9, gamma: float = GAMMA) -> np.ndarray:
     one = np.ones_like(x)
     return conserved(rho * one, u * one, v * one, p * one, gamma)

@@ -115,3 +115,24 @@ def test_context_needs_a_gpu():
         pytest.skip("GPU present")
     with pytest.raises(RuntimeError):
         _native.Context(_native.Config())
+
+
+def test_batch_init_rejects_unsupported_options(lib):
+    from paper_1709_01619_gb300 import _native
+    ok = _native.Config(eqn=1, nx=8, ny=8, p=2)
+    bad = [
+        _native.Config(eqn=1, nx=8, ny=8, p=2, limiter=1),
+        _native.Config(eqn=1, nx=8, ny=8, p=2, dtype=1),
+        _native.Config(eqn=1, nx=8, ny=8, p=2, pts=1),
+        _native.Config(eqn=1, nx=8, ny=8, p=2, div=1),
+        _native.Config(eqn=1, nx=0, ny=8, p=2),
+    ]
+    for b in bad:
+        arr = (_native._Config * 2)(ok._c(), b._c())
+        h = ctypes.c_void_p()
+        assert lib.cpr_batch_init(arr, 2, None, ctypes.byref(h)) == _native.CPR_EINVAL
+        assert not h.value and lib.cpr_batch_last_error(None)
+    h = ctypes.c_void_p()
+    assert lib.cpr_batch_init(None, 1, None, ctypes.byref(h)) == _native.CPR_EINVAL
+    assert lib.cpr_batch_step(None, None, 1, 0.0, 0.0) == _native.CPR_EINVAL
+    lib.cpr_batch_destroy(None)

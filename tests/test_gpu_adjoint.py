@@ -1,0 +1,139 @@
+"""Discrete adjoint on the GPU: residual and RK3-step transposes against the
+FP64 oracle, a dot-product check against central differences of the GPU
+residual, and gradients through checkpointed rollouts (torch.autograd)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1709_01619_gb300 import _native as nat
+from paper_1709_01619_gb300 import adjoint, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def make(dtype=nat.F64, **kw):
+    c = nat.Config(dtype=dtype, **kw)
+    o = oracle.Config(eqn=c.eqn, nx=c.nx, ny=c.ny, p=c.p, x0=c.x0, x1=c.x1, y0=c.y0, y1=c.y1,
+                      pts=c.pts, div=c.div, flux=c.flux, ax=c.ax, ay=c.ay, gamma=c.gamma,
+                      bc_x=c.bc_x, bc_y=c.bc_y)
+    return c, o
+
+
+def rough(o, seed, noise=0.02):
+    x, y = oracle.point_coords(o)
+    q = inputs.vortex(x, y, eps=3.0, xc=0.5 * o.x1, yc=0.5 * o.y1, lx=o.x1, ly=o.y1)
+    if o.eqn == oracle.ADVECTION:
+        q = q[:1]
+    return inputs.perturbed(q, seed, noise)
+
+
+def dev(a, c):
+    return torch.tensor(np.asarray(a).reshape(c.shape), dtype=c.torch_dtype, device="cuda")
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+CASES = [(eqn, p, bc, flux) for eqn in (0, 1) for p in (1, 2, 3, 4) for bc in (0, 1)
+         for flux in ((nat.RUSANOV,) if eqn == 1 else (nat.UPWIND, nat.RUSANOV))]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"eq{c[0]}-p{c[1]}-bc{c[2]}-f{c[3]}")
+@pytest.mark.parametrize("dtype", [nat.F64, nat.F32])
+def test_residual_vjp_matches_oracle(case, dtype):
+    eqn, p, bc, flux = case
+    c, o = make(dtype, eqn=eqn, nx=11, ny=9, p=p, x1=5.5, y1=4.5, bc_x=bc, bc_y=1 - bc, flux=flux,
+                ax=0.8, ay=-0.5)
+    q = rough(o, 1)
+    w = np.random.default_rng(2).standard_normal(q.shape)
+    if dtype == nat.F32:
+        q = q.astype(np.float32).astype(np.float64)
+        w = w.astype(np.float32).astype(np.float64)
+    ref = oracle.residual_vjp(o, q, w)
+    with nat.Context(c) as ctx:
+        got = ctx.residual_vjp(dev(q, c), dev(w, c)).double().cpu().numpy()
+    assert rel(got, ref) <= (1e-12 if dtype == nat.F64 else 1e-5)
+
+
+@pytest.mark.parametrize("eqn", [0, 1])
+def test_step_vjp_matches_oracle(eqn):
+    c, o = make(nat.F64, eqn=eqn, nx=13, ny=10, p=3, x1=6.5, y1=5.0, ax=0.8, ay=-0.5)
+    q = rough(o, 3)
+    w = np.random.default_rng(4).standard_normal(q.shape)
+    ref = oracle.rk3_vjp(o, q, 0.01, w)
+    with nat.Context(c) as ctx:
+        got = ctx.step_vjp(dev(q, c), dev(w, c), 0.01).cpu().numpy()
+        # cotangent arrays may alias
+        wa = dev(w, c)
+        ctx.step_vjp(dev(q, c), wa, 0.01, wa)
+        assert rel(wa.cpu().numpy(), ref) <= 1e-12
+    assert rel(got, ref) <= 1e-12
+
+
+def test_vjp_dot_product_with_gpu_residual_differences():
+    c, o = make(nat.F64, eqn=1, nx=10, ny=12, p=2, x1=5.0, y1=6.0, bc_x=1)
+    q = dev(rough(o, 5), c)
+    rng = np.random.default_rng(6)
+    with nat.Context(c) as ctx:
+        for _ in range(3):
+            v = dev(rng.standard_normal(c.shape), c)
+            w = dev(rng.standard_normal(c.shape), c)
+            h = 1e-6
+            jv = (ctx.residual(q + h * v) - ctx.residual(q - h * v)) / (2 * h)
+            lhs = float((jv * w).sum())
+            rhs = float((v * ctx.residual_vjp(q, w)).sum())
+            assert abs(lhs - rhs) <= 1e-7 * abs(rhs)
+
+
+def test_rollout_gradient_matches_central_differences():
+    c, _ = make(nat.F64, eqn=1, nx=12, ny=10, p=3, x1=10.0, y1=8.0, cfl=0.08)
+    with nat.Context(c) as ctx:
+        x, y = ctx.point_coords()
+        q0 = torch.tensor(inputs.vortex(x, y, eps=4.0, xc=5.0, yc=4.0, ly=8.0), device="cuda")
+        qt = torch.tensor(inputs.vortex(x, y, eps=3.5, xc=5.0, yc=4.0, ly=8.0), device="cuda")
+        W = adjoint.quadrature_weights(ctx)
+        nsteps, dt = 10, 0.01
+
+        def J(q):
+            qN = adjoint.rollout(q, ctx, nsteps, dt, every=4)
+            return 0.5 * (W * (qN - qt) ** 2).sum()
+
+        q0r = q0.clone().requires_grad_(True)
+        J(q0r).backward()
+        g = q0r.grad
+        rng = np.random.default_rng(7)
+        for _ in range(4):
+            d = torch.tensor(rng.standard_normal(c.shape), device="cuda")
+            h = 1e-5
+            with torch.no_grad():
+                fd = (J(q0 + h * d) - J(q0 - h * d)) / (2 * h)
+            assert float((g * d).sum()) == pytest.approx(float(fd), rel=1e-6)
+
+
+def test_fp32_gradient_against_oracle_adjoint_16x16():
+    """FP32 gradient of the misfit through 8 steps vs the FP64 oracle's
+    discrete adjoint chain on 16 x 16, p = 3."""
+    c, o = make(nat.F32, eqn=1, nx=16, ny=16, p=3, x1=10.0, y1=10.0)
+    x, y = oracle.point_coords(o)
+    q0 = inputs.vortex(x, y, eps=5.0).astype(np.float32).astype(np.float64)
+    qt = inputs.vortex(x, y, eps=4.5)
+    nsteps, dt = 8, 0.01
+    states = [q0]
+    for _ in range(nsteps):
+        states.append(oracle.rk3_step(o, states[-1], dt))
+    t = oracle.tables(3, oracle.GAUSS)
+    hx = hy = 10.0 / 16
+    Wp = (hx * hy / 4) * np.outer(t["w"], t["w"]).reshape(16)
+    gbar = Wp[None, None, :] * (states[-1] - qt)
+    for s in reversed(range(nsteps)):
+        gbar = oracle.rk3_vjp(o, states[s], dt, gbar)
+    with nat.Context(c) as ctx:
+        q0d = dev(q0, c).requires_grad_(True)
+        qN = adjoint.rollout(q0d, ctx, nsteps, dt, every=3)
+        W = adjoint.quadrature_weights(ctx)
+        (0.5 * (W * (qN - dev(qt, c)) ** 2).sum()).backward()
+        g = q0d.grad.double().cpu().numpy()
+    assert rel(g, gbar) <= 1e-4

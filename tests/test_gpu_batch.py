@@ -1,0 +1,116 @@
+"""Batched solver (cpr_batch_*) against single-problem contexts and the FP64
+oracle: uneven grids and orders p = 1..4 in one batch, fixed and per-instance
+CFL steps, odd and even step counts (FP32 increment form), autotuning."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1709_01619_gb300 import _native as nat
+from paper_1709_01619_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(9, 7, 1, 3.0), (13, 11, 2, 5.0), (16, 16, 3, 4.0), (10, 13, 4, 2.0), (24, 8, 3, 1.5)]
+
+
+def cfgs(dtype):
+    out = []
+    for i, (nx, ny, p, _) in enumerate(SHAPES):
+        h = 0.4 + 0.1 * i  # element size differs between instances
+        cfl = {1: 0.2, 2: 0.1, 3: 0.08, 4: 0.06}[p]  # stable SSP-RK3 CFL per order
+        out.append(nat.Config(eqn=nat.EULER, nx=nx, ny=ny, p=p, x1=nx * h, y1=ny * h, cfl=cfl,
+                              dtype=dtype))
+    return out
+
+
+def initial(c, eps):
+    with nat.Context(c) as ctx:
+        x, y = ctx.point_coords()
+    q = inputs.vortex(x, y, eps=eps, xc=0.5 * c.x1, yc=0.5 * c.y1, lx=c.x1, ly=c.y1)
+    return torch.tensor(q, dtype=c.torch_dtype, device="cuda")
+
+
+def rel(a, b):
+    a, b = a.double(), b.double()
+    return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+
+
+TOL = {nat.F64: 1e-12, nat.F32: 2e-6}
+
+
+def singles(cs, q0s, nsteps, dt, t_end=0.0):
+    res, times = [], []
+    for c, q0 in zip(cs, q0s):
+        with nat.Context(c) as ctx:
+            q = q0.clone()
+            ctx.step(q, nsteps, dt, t_end)
+            res.append(q)
+            times.append(ctx.get_time())
+    return res, times
+
+
+@pytest.mark.parametrize("dtype", [nat.F64, nat.F32])
+@pytest.mark.parametrize("nsteps", [1, 2, 5])
+def test_batch_matches_single_contexts(dtype, nsteps):
+    cs = cfgs(dtype)
+    q0s = [initial(c, s[3]) for c, s in zip(cs, SHAPES)]
+    ref, _ = singles(cs, q0s, nsteps, 0.004)
+    with nat.Batch(cs) as b:
+        qs = [q.clone() for q in q0s]
+        b.step(qs, nsteps, 0.004)
+        for i, (q, r) in enumerate(zip(qs, ref)):
+            assert rel(q, r) <= TOL[dtype], i
+            assert b.get_time(i)[1] == nsteps
+
+
+def test_batch_matches_oracle_fp64():
+    cs = cfgs(nat.F64)[:3]
+    with nat.Batch(cs) as b:
+        q0s = [initial(c, s[3]) for c, s in zip(cs, SHAPES)]
+        qs = [q.clone() for q in q0s]
+        b.step(qs, 3, 0.005)
+    for c, q0, q in zip(cs, q0s, qs):
+        o = oracle.Config(eqn=oracle.EULER, nx=c.nx, ny=c.ny, p=c.p, x1=c.x1, y1=c.y1)
+        q_or, _, _ = oracle.run(o, q0.cpu().numpy(), 3, 0.005)
+        assert np.linalg.norm(q.cpu().numpy() - q_or) / np.linalg.norm(q_or) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype", [nat.F64, nat.F32])
+def test_batch_cfl_steps_per_instance_to_t_end(dtype):
+    cs = cfgs(dtype)
+    # a smooth periodic solution: rounding differences between the two paths
+    # are not amplified by the flow (a vortex cut off by the small periodic
+    # boxes develops sharp fronts)
+    q0s = []
+    for c in cs:
+        with nat.Context(c) as ctx:
+            x, y = ctx.point_coords()
+        q0s.append(torch.tensor(inputs.entropy_wave(x, y, c.x1, c.y1), dtype=c.torch_dtype, device="cuda"))
+    t_end = 0.3
+    ref, times = singles(cs, q0s, 200, 0.0, t_end)
+    with nat.Batch(cs) as b:
+        qs = [q.clone() for q in q0s]
+        b.step(qs, 200, 0.0, t_end)
+        for i in range(len(cs)):
+            t, n = b.get_time(i)
+            assert t == t_end and n == times[i][1]
+            assert rel(qs[i], ref[i]) <= TOL[dtype]
+    assert len(set(n for _, n in times)) > 1  # the instances took different step counts
+
+
+def test_batch_tune_keeps_states_and_results():
+    cs = cfgs(nat.F32)
+    q0s = [initial(c, s[3]) for c, s in zip(cs, SHAPES)]
+    with nat.Batch(cs) as b:
+        qs = [q.clone() for q in q0s]
+        choices = b.tune(qs)
+        assert {p for p, _, _ in choices} == {1, 2, 3, 4}
+        assert all(f in (0, 1) and g >= 1 for _, f, g in choices)
+        for q, q0 in zip(qs, q0s):
+            assert torch.equal(q, q0)
+        assert b.get_time(0) == (0.0, 0)
+        b.step(qs, 4, 0.004)
+    ref, _ = singles(cs, q0s, 4, 0.004)
+    for q, r in zip(qs, ref):
+        assert rel(q, r) <= TOL[nat.F32]
