@@ -14,11 +14,11 @@ averages against the exact solution (which at t = 10 equals the initial field).
 summed over ranks (each rank solves its own replica; no data-path collective).
 L2 is flushed (a 256 MiB write) before every timed solve, outside its events.
 The roofline object covers the dominant kernel (the fused residual + RK stage
-kernel): algorithmic bytes per launch (the FP32 increment form moves 10 state
-arrays per RK3 step -- q, B1 | q, B1, B2 | q, B2, lo, hi', lo' -- so 10/3 * 4
-variables * 4 B = 53.3 B per point and stage on average) over its mean launch
-duration; a second roofline block repeats this on a 1024 x 1024 vortex whose
-state (268 MB per array) is larger than L2.
+kernel): algorithmic bytes per launch (8 state arrays per RK3 step: 8/3 * 4
+variables * 4 B = 42.7 B per point and stage) over its mean launch duration;
+the FP32 compensated increment form actually moves 10 arrays per step (53.3 B),
+reported as moved_gbs.  A second roofline block repeats this on a 1024 x 1024
+vortex whose state (268 MB per array) is larger than L2.
 """
 from __future__ import annotations
 
@@ -41,10 +41,15 @@ METRIC = "CPR DOF-stage updates/s (FP32 vs FP64, equal L2 error) and % HBM roofl
 UNIT = "DOF-stage/s"
 NX, P, L, EPS, T_END, CFL = 128, 3, 10.0, 5.0, 10.0, 0.08
 HBM_NX, HBM_STEPS = 1024, 20
-# State-array reads + writes per RK3 step of the FP32 path (increment form,
-# no limiter): stage 1 reads q, writes B1; stage 2 reads q, B1, writes B2;
-# stage 3 reads q, B2 and the low part, writes the new high and low parts.
-STATE_ARRAYS_PER_STEP = 10
+# Algorithmic bytes of one DOF-stage (one solution point, all 4 variables):
+# the method reads the stage state and writes the next one, and stages 2-3
+# also read q^n -- 8 state arrays per RK3 step, 8/3 * 4 variables * 4 B =
+# 42.7 B in FP32.  The FP32 path moves more: its compensated increment form
+# (stage 1 reads q, writes B1; stage 2 reads q, B1, writes B2; stage 3 reads
+# q, B2 and the low part, writes the new high and low parts) moves 10 arrays
+# per step (53.3 B per DOF-stage); both are reported.
+ALGO_ARRAYS_PER_STEP = 8
+MOVED_ARRAYS_PER_STEP = 10
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -245,10 +250,12 @@ def hbm_case(make, peak, steps=HBM_STEPS):
     msH = eh[0].elapsed_time(eh[1])
     dofH = HBM_NX * HBM_NX * (P + 1) ** 2
     launchH = msH / (3 * steps)
-    achievedH = dofH * 16 * STATE_ARRAYS_PER_STEP / 3.0 / (launchH * 1e-3) / 1e9
+    achievedH = dofH * 16 * ALGO_ARRAYS_PER_STEP / 3.0 / (launchH * 1e-3) / 1e9
+    movedH = achievedH * MOVED_ARRAYS_PER_STEP / ALGO_ARRAYS_PER_STEP
     ctxH.close()
     return {"workload": "euler_vortex_1024x1024_p3_fp32", "bound": "hbm", "achieved": achievedH,
-            "peak": peak, "unit": "GB/s", "frac": achievedH / peak, "launch_ms": launchH,
+            "peak": peak, "unit": "GB/s", "frac": achievedH / peak,
+            "moved_gbs": movedH, "moved_frac": movedH / peak, "launch_ms": launchH,
             "dof_stage_per_s": dofH * 3 * steps / (msH * 1e-3), "rk3_steps": steps}
 
 
@@ -279,7 +286,7 @@ def batch_case(peak, steps=100, warmup=3):
         torch.cuda.synchronize()
         ms = ev[0].elapsed_time(ev[1])
     rate = dof * 3 * steps / (ms * 1e-3)
-    achieved = rate * 16 * STATE_ARRAYS_PER_STEP / 3.0 / 1e9
+    achieved = rate * 16 * ALGO_ARRAYS_PER_STEP / 3.0 / 1e9
     return {"workload": "batch_64_vortex_N32-256_p2-4_fp32", "instances": len(cfgs), "dof": dof,
             "rk3_steps": steps, "ms": ms, "dof_stage_per_s": rate, "bound": "hbm",
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -355,7 +362,7 @@ def run_cpr(args, world, rank, local):
 
     # dominant kernel: fused residual + stage, 3 launches per RK3 step
     launch_ms = ms / (args.steps * 3 * nsteps)
-    bytes_per_launch = dof * 4 * 4 * STATE_ARRAYS_PER_STEP / 3.0
+    bytes_per_launch = dof * 4 * 4 * ALGO_ARRAYS_PER_STEP / 3.0
     achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
 
     if args.quick:
@@ -428,7 +435,7 @@ def run_cpr(args, world, rank, local):
         "speedup_f32_over_f64": value / world / value64 if value64 > 0 else None,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes},
-        "gpu_launches": args.steps * (3 * nsteps + 2),
+        "gpu_launches": args.steps * (3 * nsteps + 3),
         "clocks": clk,
         "cpu_baseline": cpu,
     }

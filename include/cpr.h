@@ -207,8 +207,9 @@ cpr_status cpr_step_vjp(cpr_ctx* ctx, const void* q_dev, const void* qbar_out_de
 /* ---- batches ------------------------------------------------------------
  * Many independent problems of uneven size and order advanced together (no
  * counterpart in the paper's single-grid runs).  For every SSP-RK3 stage
- * there is one persistent launch per polynomial order present in the batch;
- * each launch walks the tiles of all instances of that order.  Each
+ * there is one launch per polynomial order present in the batch; it covers
+ * the tiles of all instances of that order, either one CTA per tile or a
+ * persistent grid whose CTAs walk the tile list (the autotuner picks).  Each
  * instance keeps its own simulated time and CFL step.  All instances share
  * eqn, dtype and flux; batches run Gauss points, the LP divergence and no
  * limiter (CPR_EINVAL otherwise).  FP32 batches use the compensated
@@ -229,11 +230,12 @@ const char* cpr_batch_last_error(const cpr_batch* b);
 cpr_status cpr_batch_step(cpr_batch* b, void* const* q_devs, int nsteps, double dt_fixed, double t_end);
 
 /* Autotuner: for each order group, times one RK3 step for each tile family
- * (8x8 and 16x4 elements per CTA) and each persistent grid of 1..max
- * resident CTAs per SM, and keeps the fastest.  The states q_devs are not
- * modified and the simulated times are kept.  choices (nullable) receives 3
- * ints per group: p, family, grid size; *ngroups (nullable) the group
- * count (at most 4).  Synchronises. */
+ * (8x8 and 16x4 elements per CTA) with one CTA per tile and with each
+ * persistent grid of 1..max resident CTAs per SM smaller than that, and
+ * keeps the fastest.  The states q_devs are not modified and the simulated
+ * times are kept.  choices (nullable) receives 3 ints per group: p, family,
+ * grid size (equal to the group's tile count for one CTA per tile);
+ * *ngroups (nullable) the group count (at most 4).  Synchronises. */
 cpr_status cpr_batch_tune(cpr_batch* b, void* const* q_devs, int* choices, int* ngroups);
 
 /* Simulated time and steps of instance i (synchronises); set the time of

@@ -49,15 +49,67 @@ struct BatchArgs {
     Tab<T> tab;        // operator tables of the group's order
 };
 
-// Register budget: one resident CTA fewer than the single-problem kernel
-// (the work-list bookkeeping needs the room).
+// Register budget: as the single-problem kernel.
 template <class T, int N>
 constexpr int batch_min_blocks()
 {
-    return stage_min_blocks<T, N>() > 1 ? stage_min_blocks<T, N>() - 1 : 1;
+    return stage_min_blocks<T, N>();
 }
 
+// One work item (tile w of the group's list): thread 0 finds its instance
+// and fills the stage arguments in shared memory, then the CTA runs the tile.
 template <class T, int P, int EQ, int DIV, int FLUX, int TX, int TY, bool DELTA>
+__device__ __forceinline__ void batch_item(const BatchArgs<T>& B, int w, StageArgs<T>& sA, int& s_t, int& s_n,
+                                           unsigned char* smem_raw)
+{
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = B.ninst - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (B.inst[mid].tile0 <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchInst<T>& I = B.inst[lo];
+        StageArgs<T>& A = sA;
+        A.npts = I.npts;
+        A.nx = I.nx;
+        A.ny = I.ny;
+        A.bcx = I.bcx;
+        A.bcy = I.bcy;
+        A.tiles_x = I.tiles_x;
+        A.mode = B.mode;
+        A.do_avg = 0;
+        A.avg = nullptr;
+        A.do_wave = B.mode == MODE_SO3 || B.mode == MODE_INC3;
+        A.wave = I.wave;
+        A.ctrl = I.ctrl;
+        A.rhx2 = I.rhx2;
+        A.rhy2 = I.rhy2;
+        A.ph = I.ph;
+        A.qb = nullptr;
+        A.qn = nullptr;
+        A.lo = I.lo;
+        T* hiq = B.swap ? I.Y : I.X;
+        T* other = B.swap ? I.X : I.Y;
+        switch (B.mode) {
+        case MODE_SO1: A.qs = I.X; A.out = I.Y; break;
+        case MODE_SO2: A.qs = I.Y; A.qn = I.X; A.out = I.Z; break;
+        case MODE_SO3: A.qs = I.Z; A.qn = I.X; A.out = I.X; break;
+        case MODE_INC1: A.qs = hiq; A.out = other; break;
+        case MODE_INC2: A.qs = hiq; A.qb = other; A.out = I.Z; break;
+        default: A.qs = hiq; A.qb = I.Z; A.out = other; break;
+        }
+        s_t = w - I.tile0;
+        s_n = I.ntiles;
+    }
+    __syncthreads();
+    stage_tile<T, P, EQ, DIV, FLUX, TX, TY, DELTA>(sA, B.tab, s_t, threadIdx.x, smem_raw, s_t, s_n);
+}
+
+// PERSIST: CTAs walk the work list with a grid stride; otherwise the grid
+// has one CTA per work item.  The loop costs registers (the tile body spills
+// more inside it), so the autotuner weighs both forms.
+template <class T, int P, int EQ, int DIV, int FLUX, int TX, int TY, bool DELTA, bool PERSIST>
 __global__ void __launch_bounds__(TX * TY * (P + 1), (batch_min_blocks<T, P + 1>()))
 cpr_batch_stage_kernel(const BatchArgs<T> B)
 {
@@ -66,50 +118,13 @@ cpr_batch_stage_kernel(const BatchArgs<T> B)
     // of use instead of occupying registers through the whole tile.
     __shared__ StageArgs<T> sA;
     __shared__ int s_t, s_n;
-    for (int w = blockIdx.x; w < B.total; w += gridDim.x) {
-        if (threadIdx.x == 0) {
-            int lo = 0, hi = B.ninst - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (B.inst[mid].tile0 <= w) lo = mid;
-                else hi = mid - 1;
-            }
-            const BatchInst<T>& I = B.inst[lo];
-            StageArgs<T>& A = sA;
-            A.npts = I.npts;
-            A.nx = I.nx;
-            A.ny = I.ny;
-            A.bcx = I.bcx;
-            A.bcy = I.bcy;
-            A.tiles_x = I.tiles_x;
-            A.mode = B.mode;
-            A.do_avg = 0;
-            A.avg = nullptr;
-            A.do_wave = B.mode == MODE_SO3 || B.mode == MODE_INC3;
-            A.wave = I.wave;
-            A.ctrl = I.ctrl;
-            A.rhx2 = I.rhx2;
-            A.rhy2 = I.rhy2;
-            A.ph = I.ph;
-            A.qb = nullptr;
-            A.qn = nullptr;
-            A.lo = I.lo;
-            T* hiq = B.swap ? I.Y : I.X;
-            T* other = B.swap ? I.X : I.Y;
-            switch (B.mode) {
-            case MODE_SO1: A.qs = I.X; A.out = I.Y; break;
-            case MODE_SO2: A.qs = I.Y; A.qn = I.X; A.out = I.Z; break;
-            case MODE_SO3: A.qs = I.Z; A.qn = I.X; A.out = I.X; break;
-            case MODE_INC1: A.qs = hiq; A.out = other; break;
-            case MODE_INC2: A.qs = hiq; A.qb = other; A.out = I.Z; break;
-            default: A.qs = hiq; A.qb = I.Z; A.out = other; break;
-            }
-            s_t = w - I.tile0;
-            s_n = I.ntiles;
+    if constexpr (PERSIST) {
+        for (int w = blockIdx.x; w < B.total; w += gridDim.x) {
+            batch_item<T, P, EQ, DIV, FLUX, TX, TY, DELTA>(B, w, sA, s_t, s_n, smem_raw);
+            __syncthreads();
         }
-        __syncthreads();
-        stage_tile<T, P, EQ, DIV, FLUX, TX, TY, DELTA>(sA, B.tab, s_t, threadIdx.x, smem_raw, s_t, s_n);
-        __syncthreads();
+    } else {
+        batch_item<T, P, EQ, DIV, FLUX, TX, TY, DELTA>(B, blockIdx.x, sA, s_t, s_n, smem_raw);
     }
 }
 

@@ -35,7 +35,7 @@ struct Group {
     void* d_inst[cpr::kBatchFamilies] = {nullptr, nullptr};
     void* h_inst[cpr::kBatchFamilies] = {nullptr, nullptr};  // pinned mirrors
     int fam = 0;                              // chosen tile family
-    int grid = 0;                             // chosen persistent grid
+    int grid = 0;                             // chosen grid (= total: one CTA per tile)
     int occ[cpr::kBatchFamilies] = {0, 0};    // resident CTAs per SM
 };
 
@@ -244,7 +244,7 @@ cudaError_t group_occupancy(cpr_batch* b, Group& g)
         g.occ[fam] = std::max(1, g.occ[fam]);
     }
     g.fam = 0;
-    g.grid = std::min(g.total[0], b->sms * g.occ[0]);
+    g.grid = g.total[0];  // untuned: one CTA per tile
     return cudaSuccess;
 }
 
@@ -513,9 +513,9 @@ extern "C" cpr_status cpr_batch_set_time(cpr_batch* b, double t, long long steps
 }
 
 // Autotuner: for every order group, time one RK3 step of that group (the
-// stages that leave the caller's arrays untouched) for every tile family and
-// every persistent-grid size of 1..occupancy CTAs per SM, and keep the
-// fastest.  The time-control blocks are saved and restored around the runs.
+// stages that leave the caller's arrays untouched) for every tile family,
+// with one CTA per tile and with every persistent grid of 1..occupancy CTAs
+// per SM that is smaller than that, and keep the fastest.  The time-control blocks are saved and restored around the runs.
 extern "C" cpr_status cpr_batch_tune(cpr_batch* b, void* const* q, int* choices, int* ngroups)
 {
     if (!b) return CPR_EINVAL;
@@ -536,8 +536,10 @@ extern "C" cpr_status cpr_batch_tune(cpr_batch* b, void* const* q, int* choices,
         float best = 1e30f;
         int best_fam = g.fam, best_grid = g.grid;
         for (int fam = 0; fam < cpr::kBatchFamilies; ++fam)
-            for (int c = 1; c <= g.occ[fam]; ++c) {
-                const int grid = std::min(g.total[fam], b->sms * c);
+            for (int c = 0; c <= g.occ[fam]; ++c) {
+                // c = 0: one CTA per tile; c >= 1: persistent grid of c CTAs per SM
+                if (c > 0 && b->sms * c >= g.total[fam]) break;
+                const int grid = c == 0 ? g.total[fam] : b->sms * c;
                 auto run = [&]() -> cudaError_t {
                     const int nm = b->use_inc ? 3 : 2;
                     for (int m = 0; m < nm; ++m) {

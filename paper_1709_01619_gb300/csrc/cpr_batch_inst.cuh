@@ -13,11 +13,18 @@ static cudaError_t batch_one(const BatchArgs<T>& B, int grid, cudaStream_t s, in
     constexpr int N = P + 1, V = NVars<EQ>::value;
     constexpr int TX = BatchTile<FAM>::X, TY = BatchTile<FAM>::Y;
     constexpr int NT = TX * TY * N;
-    auto kern = cpr_batch_stage_kernel<T, P, EQ, DIV_LP, FLUX, TX, TY, sizeof(T) == 4>;
-    const size_t smem = sizeof(T) * StageLayout<N, V, TX, TY>::TOTAL;
-    if (what == 1) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (what == 2) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, NT, smem);
-    kern<<<grid, NT, smem, s>>>(B);
+    auto loop = cpr_batch_stage_kernel<T, P, EQ, DIV_LP, FLUX, TX, TY, stage_delta<T>(), true>;
+    auto flat = cpr_batch_stage_kernel<T, P, EQ, DIV_LP, FLUX, TX, TY, stage_delta<T>(), false>;
+    const size_t smem = sizeof(T) * StageLayout<N, V, TX, TY, stage_delta<T>()>::TOTAL;
+    if (what == 1) {
+        cudaError_t e = cudaFuncSetAttribute(loop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(flat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    if (what == 2) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, loop, NT, smem);
+    // a grid as large as the work list takes the one-tile-per-CTA form
+    if (grid >= B.total) flat<<<B.total, NT, smem, s>>>(B);
+    else loop<<<grid, NT, smem, s>>>(B);
     return cudaGetLastError();
 }
 

@@ -73,25 +73,33 @@ struct Phys {
     T ax, ay; // advection
 };
 
-__device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
-__device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
-
-// Reciprocal and square root inside the FP32 flux differences: the
-// hardware approximations (at most 2 ulp), whose error enters only through
-// quantities that multiply small differences.  FP64 keeps IEEE operations.
+// Reciprocal and square root in the FP32 physics (1/rho, sound speed): the
+// hardware approximations (a few ulp), at the level of the rounding of the
+// flux itself.  FP64 keeps IEEE operations.
 __device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ float fsqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : sqrtf(x); }
+__device__ __forceinline__ float fsqrt(float x)
+{
+    // 0 -> 0, negative -> NaN, otherwise x / sqrt(x) from the approximate rsqrt
+    return x >= 0.0f ? x * rsqrtf(fmaxf(x, 1.17549435e-38f)) : __int_as_float(0x7fffffff);
+}
 __device__ __forceinline__ double fsqrt(double x) { return sqrt(x); }
 
 // Pressure, Eq. 5: p = (gamma - 1)(e - (rho u u + rho v v)/2) with u = rho u / rho.
+// Also returns r = 1 / rho.
 template <class T>
-__device__ __forceinline__ T pressure(const T* q, T gamma, T& u, T& v)
+__device__ __forceinline__ T pressure(const T* q, T gamma, T& u, T& v, T& r)
 {
-    T r = T(1) / q[0];
+    r = frcp(q[0]);
     u = q[1] * r;
     v = q[2] * r;
     return (gamma - T(1)) * (q[3] - T(0.5) * (q[1] * u + q[2] * v));
+}
+template <class T>
+__device__ __forceinline__ T pressure(const T* q, T gamma, T& u, T& v)
+{
+    T r;
+    return pressure(q, gamma, u, v, r);
 }
 
 // x-flux f(q) and y-flux g(q) of Eq. 4.
@@ -133,9 +141,8 @@ __device__ __forceinline__ void flux_jvp(const T* q, const T* dq, const Phys<T>&
     if constexpr (EQ == EQ_ADV) {
         df[0] = (DIR == 0 ? ph.ax : ph.ay) * dq[0];
     } else {
-        T u, v;
-        T p = pressure(q, ph.gamma, u, v);
-        T r = T(1) / q[0];
+        T u, v, r;
+        T p = pressure(q, ph.gamma, u, v, r);
         T vn = DIR == 0 ? u : v;
         T dvn = ((DIR == 0 ? dq[1] : dq[2]) - vn * dq[0]) * r;
         T dp = (ph.gamma - T(1)) * (dq[3] - (u * dq[1] + v * dq[2]) + T(0.5) * (u * u + v * v) * dq[0]);
@@ -162,13 +169,13 @@ __device__ __forceinline__ void common_flux(const T* qm, const T* qp, const Phys
             F[0] = T(0.5) * (an * qm[0] + an * qp[0]) - T(0.5) * lam * (qp[0] - qm[0]);
         }
     } else {
-        T um, vm, up, vp;
-        T pm = pressure(qm, ph.gamma, um, vm);
-        T pp = pressure(qp, ph.gamma, up, vp);
+        T um, vm, up, vp, rm, rp;
+        T pm = pressure(qm, ph.gamma, um, vm, rm);
+        T pp = pressure(qp, ph.gamma, up, vp, rp);
         T vnm = DIR == 0 ? um : vm;
         T vnp = DIR == 0 ? up : vp;
-        T sm = (vnm >= T(0) ? vnm : -vnm) + dsqrt(ph.gamma * pm / qm[0]);
-        T sp = (vnp >= T(0) ? vnp : -vnp) + dsqrt(ph.gamma * pp / qp[0]);
+        T sm = (vnm >= T(0) ? vnm : -vnm) + fsqrt(ph.gamma * pm * rm);
+        T sp = (vnp >= T(0) ? vnp : -vnp) + fsqrt(ph.gamma * pp * rp);
         T lam = sm >= sp ? sm : sp;
         T Fm[4], Fp[4];
         Fm[0] = qm[0] * vnm;
@@ -189,11 +196,11 @@ template <int EQ, class T>
 __device__ __forceinline__ T point_speed(const T* q, const Phys<T>& ph)
 {
     if constexpr (EQ == EQ_ADV) {
-        return dsqrt(ph.ax * ph.ax + ph.ay * ph.ay);
+        return fsqrt(ph.ax * ph.ax + ph.ay * ph.ay);
     } else {
-        T u, v;
-        T p = pressure(q, ph.gamma, u, v);
-        return dsqrt(u * u + v * v) + dsqrt(ph.gamma * p / q[0]);
+        T u, v, r;
+        T p = pressure(q, ph.gamma, u, v, r);
+        return fsqrt(u * u + v * v) + fsqrt(ph.gamma * p * r);
     }
 }
 
@@ -318,7 +325,7 @@ __device__ __forceinline__ void flux_vjp(const T* q, const T* w, const Phys<T>& 
         qbar[0] += (DIR == 0 ? ph.ax : ph.ay) * w[0];
     } else {
         const T g1 = ph.gamma - T(1);
-        const T r = q[0], ir = T(1) / r;
+        const T r = q[0], ir = frcp(r);
         const T u = q[1] * ir, v = q[2] * ir;
         const T p = g1 * (q[3] - T(0.5) * (q[1] * u + q[2] * v));
         const T vn = DIR == 0 ? u : v;
@@ -339,16 +346,16 @@ template <int DIR, class T>
 __device__ __forceinline__ void speed_grad(const T* q, const Phys<T>& ph, T* gs)
 {
     const T g1 = ph.gamma - T(1);
-    const T r = q[0], ir = T(1) / r;
+    const T r = q[0], ir = frcp(r);
     const T u = q[1] * ir, v = q[2] * ir;
     const T p = g1 * (q[3] - T(0.5) * (q[1] * u + q[2] * v));
-    const T cs = dsqrt(ph.gamma * p * ir);
+    const T cs = fsqrt(ph.gamma * p * ir);
     const T vn = DIR == 0 ? u : v;
     const T sg = vn >= T(0) ? T(1) : T(-1);
     const T nx = DIR == 0 ? T(1) : T(0), ny = DIR == 0 ? T(0) : T(1);
     const T dvn[4] = {-vn * ir, nx * ir, ny * ir, T(0)};
     const T dpq[4] = {g1 * T(0.5) * (u * u + v * v), -g1 * u, -g1 * v, g1};
-    const T k = ph.gamma / (T(2) * cs * r);
+    const T k = ph.gamma * frcp(T(2) * cs * r);
 #pragma unroll
     for (int m = 0; m < 4; ++m) gs[m] = sg * dvn[m] + k * (dpq[m] - (m == 0 ? p * ir : T(0)));
 }
@@ -380,12 +387,12 @@ __device__ __forceinline__ void common_flux_vjp(const T* qm, const T* qp, const 
         }
         flux_vjp<EQ, DIR>(qm, hw, ph, qbm);
         flux_vjp<EQ, DIR>(qp, hw, ph, qbp);
-        T um, vm, up, vp;
-        const T pm = pressure(qm, ph.gamma, um, vm);
-        const T pp = pressure(qp, ph.gamma, up, vp);
+        T um, vm, up, vp, rm, rp;
+        const T pm = pressure(qm, ph.gamma, um, vm, rm);
+        const T pp = pressure(qp, ph.gamma, up, vp, rp);
         const T vnm = DIR == 0 ? um : vm, vnp = DIR == 0 ? up : vp;
-        const T sm = (vnm >= T(0) ? vnm : -vnm) + dsqrt(ph.gamma * pm / qm[0]);
-        const T sp = (vnp >= T(0) ? vnp : -vnp) + dsqrt(ph.gamma * pp / qp[0]);
+        const T sm = (vnm >= T(0) ? vnm : -vnm) + fsqrt(ph.gamma * pm * rm);
+        const T sp = (vnp >= T(0) ? vnp : -vnp) + fsqrt(ph.gamma * pp * rp);
         const T lam = sm >= sp ? sm : sp;
         T jump = T(0);
 #pragma unroll

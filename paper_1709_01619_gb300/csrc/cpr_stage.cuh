@@ -23,22 +23,23 @@
 // f(q_ref + d) - f(q_ref) from the state q_ref at point (0, 0) of its element.
 // The divergence and the edge terms only need flux differences (the rows of
 // D sum to zero, the edge weights sum to one), so the rounding error of the
-// O(1) flux values drops out.  The common flux on a face is formed relative
-// to the lower (left/bottom) element's reference; the upper element shifts it
-// by f(ref_upper) - f(ref_lower), one value per face.  FP64 evaluates the
-// fluxes directly (reference zero).
+// O(1) flux values drops out.  The common flux on a face inside the tile is
+// formed relative to the upper (right/top) element's reference and shifted by
+// f(ref_upper) - f(ref_lower) for the lower element's jump; on the tile's
+// right/top edge it is formed relative to the lower element's reference.
+// FP64 evaluates the fluxes directly (reference zero).
 //
-// Phases (one barrier after each):
-//   1 rows of the stage state into shared memory, element references; halo
+// Phases (one barrier after each of 1-3):
+//   1 own row: into the tile copy, x-line (flux differences, d/dxi, edge
+//     states and fluxes; the right edge values go to shared memory); halo
 //     lines (the edge states of the neighbour elements facing the tile)
 //     straight from L2
-//   2 x-lines and y-lines: flux differences, d/dxi and d/deta, edge states,
-//     flux shifts to the left and lower neighbours' references
-//   3 each thread: common flux on its element's left and lower face point
-//     (plus the right / upper face for the tile's last column / row), one
-//     evaluation per face point; the neighbour's copy goes to shared memory
-//   4 y-lines: y-part of R into a shared accumulator (over the dead tile copy)
-//   5 x-lines: x-part of R, stage update, store; optional fused element
+//   2 y-line of column k from the tile copy: d/deta, edge states and fluxes
+//   3 d/deta into the dead tile copy; common flux on the element's left and
+//     lower face points, one evaluation per face point, giving the jumps
+//     F* - f of both elements; the tile's right / upper edge faces go to
+//     dedicated threads (no divergent tail in every warp)
+//   4 row k: x- and y-parts of R, stage update, store; optional fused element
 //     averages (Algorithm 9) and max signal speed of the result.
 #pragma once
 
@@ -68,30 +69,43 @@ struct StageArgs {
     Tab<T> tab;
 };
 
-template <int N, int V, int TX, int TY>
+template <int N, int V, int TX, int TY, bool DELTA>
 struct StageLayout {
     static constexpr int NN = N * N;
-    // element stride in the tile arrays: a multiple of 4 (16-byte rows) that
-    // spreads the column reads of neighbouring elements over the banks
-    static constexpr int ES = (NN % 4 == 0) ? NN + 4 : ((NN + 3) / 4) * 4;
+    // N = 4: rows of 16 bytes, element stride 16 words, row b of element el
+    // stored at slot b ^ ((el >> 1) & 3).  A quarter warp's row accesses
+    // (two elements) and a warp's column reads (eight elements, one word
+    // each) then both hit distinct banks.  Other N: padded element stride.
+    static constexpr bool SWZ = N == 4;
+    static constexpr int ES = SWZ ? 16 : ((NN % 4 == 0) ? NN + 4 : ((NN + 3) / 4) * 4);
     static constexpr int E = TX * TY;
     static constexpr int PE = (TX + 2) * (TY + 2);     // tile with its halo ring
-    static constexpr int SQ = V * E * ES;              // tile copy; later the y-part of R
+    // The y-derivatives go over the dead tile copy in phase 3 (a buffer of
+    // their own, written in phase 2, holds fewer registers across the
+    // barrier but leaves too little of the SM's shared memory / L1 to L1).
+    static constexpr bool RYSEP = false;
+    static constexpr int SQ = V * E * ES;              // tile copy
+    static constexpr int RY = RYSEP ? SQ : 0;          // y-derivatives of the flux
     static constexpr int XR = V * TY * (TX + 1) * N;   // right edge states, elements -1..TX-1
     static constexpr int XH = V * TY * N;              // left edge states of the right halo
-    static constexpr int XG = V * TY * TX * N;         // common flux for the left element
-    static constexpr int YT = V * (TY + 1) * TX * N;
-    static constexpr int YH = V * TX * N;
-    static constexpr int YG = V * TY * TX * N;
-    static constexpr int RF = V * PE;                  // element reference states
-    static constexpr int TOTAL = SQ + XR + XH + XG + YT + YH + YG + RF;
-    __device__ static int sq(int v, int el, int pt) { return (v * E + el) * ES + pt; }
+    static constexpr int XF = V * E * N;               // right edge fluxes, then the right jumps
+    static constexpr int YT = V * (TY + 1) * TX * N;   // top edge states, elements -1..TY-1
+    static constexpr int YH = V * TX * N;              // bottom edge states of the upper halo
+    static constexpr int YF = V * E * N;               // top edge fluxes, then the top jumps
+    static constexpr int JB = V * E * N;               // bottom jumps
+    static constexpr int RF = DELTA ? V * PE : 0;      // element reference states
+    static constexpr int TOTAL = SQ + RY + XR + XH + XF + YT + YH + YF + JB + RF;
+    // point (b, a) (row b, column a) of element el in a tile array
+    __device__ static int sq(int v, int el, int b, int a)
+    {
+        return (v * E + el) * ES + (SWZ ? 4 * (b ^ ((el >> 1) & 3)) : b * N) + a;
+    }
     __device__ static int xr(int v, int ty, int f, int k) { return ((v * TY + ty) * (TX + 1) + f) * N + k; }
     __device__ static int xh(int v, int ty, int k) { return (v * TY + ty) * N + k; }
-    __device__ static int xg(int v, int ty, int tx, int k) { return ((v * TY + ty) * TX + tx) * N + k; }
     __device__ static int yt(int v, int g, int tx, int k) { return ((v * (TY + 1) + g) * TX + tx) * N + k; }
     __device__ static int yh(int v, int tx, int k) { return (v * TX + tx) * N + k; }
-    __device__ static int yg(int v, int ty, int tx, int k) { return ((v * TY + ty) * TX + tx) * N + k; }
+    // per-element line values (XF, YF, JB): line k of element el
+    __device__ static int ef(int v, int el, int k) { return (v * E + el) * N + k; }
     // reference of the element at tile coordinates (lx, ly), -1 <= lx <= TX
     __device__ static int rf(int v, int lx, int ly) { return v * PE + (ly + 1) * (TX + 2) + (lx + 1); }
 };
@@ -205,15 +219,25 @@ __device__ __forceinline__ void compensated_add(double& hi, double& lo, double D
     lo = 0.0;
 }
 
+// FP32 fluxes in the delta form (1) or directly (0).
+#ifndef CPR_FP32_DELTA
+#define CPR_FP32_DELTA 0
+#endif
+template <class T>
+constexpr bool stage_delta()
+{
+    return sizeof(T) == 4 && CPR_FP32_DELTA != 0;
+}
+
 // Resident CTAs per SM the register budget is sized for (FP32: as many as the
 // shared memory allows; FP64: one).
 #ifndef CPR_STAGE_MINB_FP32
-#define CPR_STAGE_MINB_FP32 3
+#define CPR_STAGE_MINB_FP32 4
 #endif
 template <class T, int N>
 constexpr int stage_min_blocks()
 {
-    return sizeof(T) == 8 ? 1 : (N <= 4 ? CPR_STAGE_MINB_FP32 : 2);
+    return sizeof(T) == 8 ? 1 : (N <= 4 ? CPR_STAGE_MINB_FP32 : 3);
 }
 
 // One tile of the stage: the work of one CTA.  tile indexes the instance's
@@ -226,17 +250,19 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
 {
     constexpr int N = P + 1, NN = N * N, V = NVars<EQ>::value;
     constexpr int NT = TX * TY * N;
-    using L = StageLayout<N, V, TX, TY>;
+    static_assert(TX * TY >= TX + TY, "every tile-edge face point needs a thread of its own");
+    using L = StageLayout<N, V, TX, TY, DELTA>;
     T* sq = reinterpret_cast<T*>(smem_raw);
-    T* rS = sq;          // y-part of R, once the tile copy is dead
-    T* xR = sq + L::SQ;
+    T* ryS = L::RYSEP ? sq + L::SQ : sq;  // y-derivatives (else over the dead tile copy)
+    T* xR = sq + L::SQ + L::RY;
     T* xH = xR + L::XR;
-    T* xG = xH + L::XH;
-    T* yT = xG + L::XG;
+    T* xF = xH + L::XH;
+    T* yT = xF + L::XF;
     T* yH = yT + L::YT;
-    T* yG = yH + L::YH;
-    T* rfS = yG + L::YG;
-    T* avS = xR;         // row partial sums of the averages, reuses xR after phase 4
+    T* yF = yH + L::YH;
+    T* jB = yF + L::YF;
+    T* rfS = jB + L::JB;
+    T* avS = xR;         // row partial sums of the averages, reuses xR after phase 3
 
     if (A.mode > 0 && A.ctrl->done) return;  // t_end reached: uniform exit
 
@@ -249,21 +275,78 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
     const bool valid = active && tx < TXe && ty < TYe;
     const long long e = (long long)(j0 + ty) * A.nx + (i0 + tx);
     const bool addb = A.mode == MODE_INC2 || A.mode == MODE_INC3;
+    const bool lwall = A.bcx && i0 + tx == 0, bwall = A.bcy && j0 + ty == 0;
 
-    // ---- phase 1: tile rows, references, halo lines -----------------------
+    // ---- phase 1: own row -> tile copy and x-line; halo lines --------------
+    T rx[N][V];           // d/dxi of the flux differences along row k
+    T eL[V], fL[V];       // own left edge state and flux
+    Ref<T> rf;            // own reference (delta form)
     if (valid) {
+        T d[N][V], q0[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
+            const T* src = A.qs + v * A.npts + e * NN;
+            const T* srb = A.qb + v * A.npts + e * NN;
             T row[N];
-            gload_row<N>(A.qs + v * A.npts + e * NN + k * N, row);
+            gload_row<N>(src + k * N, row);
             if (addb) {
                 T b[N];
-                gload_row<N>(A.qb + v * A.npts + e * NN + k * N, b);
+                gload_row<N>(srb + k * N, b);
 #pragma unroll
                 for (int a = 0; a < N; ++a) row[a] += b[a];
             }
-            sm_store_row<N>(sq + L::sq(v, el, k * N), row);
-            if (DELTA && k == 0) rfS[L::rf(v, tx, ty)] = row[0];
+            sm_store_row<N>(sq + L::sq(v, el, k, 0), row);
+            q0[v] = T(0);
+            if (DELTA) {
+                // point (0, 0) of the element, formed exactly as the halo
+                // loaders form it
+                q0[v] = k == 0 ? row[0] : (addb ? src[0] + srb[0] : src[0]);
+                if (k == 0) rfS[L::rf(v, tx, ty)] = q0[v];
+            }
+#pragma unroll
+            for (int a = 0; a < N; ++a) d[a][v] = DELTA ? row[a] - q0[v] : row[a];
+        }
+        if constexpr (DELTA) rf = make_ref<EQ>(q0, A.ph);
+        T f[N][V], col[N], eR[V], fR[V];
+#pragma unroll
+        for (int a = 0; a < N; ++a) line_flux<EQ, 0, DELTA>(rf, d[a], A.ph, f[a]);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+#pragma unroll
+            for (int l = 0; l < N; ++l) col[l] = d[l][v];
+            eL[v] = line_dot<N>(tb.lm, col);
+            eR[v] = line_dot<N>(tb.lp, col);
+        }
+        if constexpr (DIV == DIV_LP) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+#pragma unroll
+                for (int l = 0; l < N; ++l) col[l] = f[l][v];
+#pragma unroll
+                for (int a = 0; a < N; ++a) rx[a][v] = line_dot<N>(tb.D[a], col);
+                fL[v] = line_dot<N>(tb.lm, col);
+                fR[v] = line_dot<N>(tb.lp, col);
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                T dq[V], qa[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+#pragma unroll
+                    for (int l = 0; l < N; ++l) col[l] = d[l][v];
+                    dq[v] = line_dot<N>(tb.D[a], col);
+                    qa[v] = DELTA ? q0[v] + d[a][v] : d[a][v];
+                }
+                flux_jvp<EQ, 0>(qa, dq, A.ph, rx[a]);
+            }
+            line_flux<EQ, 0, DELTA>(rf, eL, A.ph, fL);
+            line_flux<EQ, 0, DELTA>(rf, eR, A.ph, fR);
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            xR[L::xr(v, ty, tx + 1, k)] = eR[v];
+            xF[L::ef(v, el, k)] = fR[v];
         }
     }
     {
@@ -316,13 +399,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
                 }
 #pragma unroll
                 for (int l = 0; l < N; ++l) line[l] -= ref;
-                const T d = line_dot<N>(coef, line);
+                const T dv = line_dot<N>(coef, line);
                 if (xdir) {
-                    if (side) xH[L::xh(v, pos, kk)] = d;
-                    else xR[L::xr(v, pos, 0, kk)] = d;
+                    if (side) xH[L::xh(v, pos, kk)] = dv;
+                    else xR[L::xr(v, pos, 0, kk)] = dv;
                 } else {
-                    if (side) yH[L::yh(v, pos, kk)] = d;
-                    else yT[L::yt(v, 0, pos, kk)] = d;
+                    if (side) yH[L::yh(v, pos, kk)] = dv;
+                    else yT[L::yt(v, 0, pos, kk)] = dv;
                 }
                 if (DELTA && kk == 0) rfS[L::rf(v, lx, ly)] = ref;
             }
@@ -330,81 +413,20 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
     }
     __syncthreads();
 
-    // walls: transmissive edges of the domain (ghost state = own edge state)
-    const bool lwall = A.bcx && i0 + tx == 0, bwall = A.bcy && j0 + ty == 0;
-    const bool redge = tx == TXe - 1, tedge = ty == TYe - 1;
-    const bool rwall = A.bcx && i0 + TXe == A.nx, twall = A.bcy && j0 + TYe == A.ny;
-
-    // ---- phase 2: line operators ----------------------------------------
-    Ref<T> rf;                      // own reference (delta form)
-    T rx[N][V], ry[N][V];           // d/dxi, d/deta of the flux differences
-    T fL[V], fR[V], gB[V], gT[V];   // edge values of the flux
-    T eL[V], eB[V];                 // own left / bottom edge states
-    T sL[V], sB[V];                 // f(ref_own) - f(ref_left), f(ref_own) - f(ref_below)
-    T oL[V], oB[V];                 // ref_left - ref_own, ref_below - ref_own
+    // ---- phase 2: y-line (column k of the element) ---------------------------
+    T ry[N][V];           // d/deta of the flux differences along column k
+    T eB[V], gB[V];       // own bottom edge state and flux
     if (valid) {
-        T q0[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) q0[v] = DELTA ? rfS[L::rf(v, tx, ty)] : T(0);
-        if constexpr (DELTA) rf = make_ref<EQ>(q0, A.ph);
-        // x-line: row k
-        T d[N][V], f[N][V], col[N];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            T row[N];
-            sm_load_row<N>(sq + L::sq(v, el, k * N), row);
-#pragma unroll
-            for (int a = 0; a < N; ++a) d[a][v] = DELTA ? row[a] - q0[v] : row[a];
-        }
-#pragma unroll
-        for (int a = 0; a < N; ++a) line_flux<EQ, 0, DELTA>(rf, d[a], A.ph, f[a]);
-        T eR[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-#pragma unroll
-            for (int l = 0; l < N; ++l) col[l] = d[l][v];
-            eL[v] = line_dot<N>(tb.lm, col);
-            eR[v] = line_dot<N>(tb.lp, col);
-        }
-        if constexpr (DIV == DIV_LP) {
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-#pragma unroll
-                for (int l = 0; l < N; ++l) col[l] = f[l][v];
-#pragma unroll
-                for (int a = 0; a < N; ++a) rx[a][v] = line_dot<N>(tb.D[a], col);
-                fL[v] = line_dot<N>(tb.lm, col);
-                fR[v] = line_dot<N>(tb.lp, col);
-            }
-        } else {
-#pragma unroll
-            for (int a = 0; a < N; ++a) {
-                T dq[V], qa[V];
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-#pragma unroll
-                    for (int l = 0; l < N; ++l) col[l] = d[l][v];
-                    dq[v] = line_dot<N>(tb.D[a], col);
-                    qa[v] = DELTA ? q0[v] + d[a][v] : d[a][v];
-                }
-                flux_jvp<EQ, 0>(qa, dq, A.ph, rx[a]);
-            }
-            line_flux<EQ, 0, DELTA>(rf, eL, A.ph, fL);
-            line_flux<EQ, 0, DELTA>(rf, eR, A.ph, fR);
-        }
-#pragma unroll
-        for (int v = 0; v < V; ++v) xR[L::xr(v, ty, tx + 1, k)] = eR[v];
-        // y-line: column k
+        T d[N][V], g[N][V], col[N], eT[V], gT[V];
 #pragma unroll
         for (int b = 0; b < N; ++b)
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                const T x = sq[L::sq(v, el, b * N + k)];
-                d[b][v] = DELTA ? x - q0[v] : x;
+                const T x = sq[L::sq(v, el, b, k)];
+                d[b][v] = DELTA ? x - rf.q[v] : x;
             }
 #pragma unroll
-        for (int b = 0; b < N; ++b) line_flux<EQ, 1, DELTA>(rf, d[b], A.ph, f[b]);
-        T eT[V];
+        for (int b = 0; b < N; ++b) line_flux<EQ, 1, DELTA>(rf, d[b], A.ph, g[b]);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
 #pragma unroll
@@ -416,7 +438,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
 #pragma unroll
             for (int v = 0; v < V; ++v) {
 #pragma unroll
-                for (int l = 0; l < N; ++l) col[l] = f[l][v];
+                for (int l = 0; l < N; ++l) col[l] = g[l][v];
 #pragma unroll
                 for (int b = 0; b < N; ++b) ry[b][v] = line_dot<N>(tb.D[b], col);
                 gB[v] = line_dot<N>(tb.lm, col);
@@ -431,7 +453,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
 #pragma unroll
                     for (int l = 0; l < N; ++l) col[l] = d[l][v];
                     dq[v] = line_dot<N>(tb.D[b], col);
-                    qb[v] = DELTA ? q0[v] + d[b][v] : d[b][v];
+                    qb[v] = DELTA ? rf.q[v] + d[b][v] : d[b][v];
                 }
                 flux_jvp<EQ, 1>(qb, dq, A.ph, ry[b]);
             }
@@ -439,105 +461,136 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
             line_flux<EQ, 1, DELTA>(rf, eT, A.ph, gT);
         }
 #pragma unroll
-        for (int v = 0; v < V; ++v) yT[L::yt(v, ty + 1, tx, k)] = eT[v];
-        // reference offsets and flux shifts to the left and lower neighbours:
-        // f(ref_own) - f(ref_nb) = -(f(ref_own + (ref_nb - ref_own)) - f(ref_own))
-        if constexpr (DELTA) {
-            T t[V];
+        for (int v = 0; v < V; ++v) {
+            yT[L::yt(v, ty + 1, tx, k)] = eT[v];
+            yF[L::ef(v, el, k)] = gT[v];
+        }
+        if constexpr (L::RYSEP) {
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                oL[v] = lwall ? T(0) : rfS[L::rf(v, tx - 1, ty)] - q0[v];
-                oB[v] = bwall ? T(0) : rfS[L::rf(v, tx, ty - 1)] - q0[v];
-            }
-            dflux<EQ, 0>(rf, oL, A.ph, t);
+            for (int b = 0; b < N; ++b)
 #pragma unroll
-            for (int v = 0; v < V; ++v) sL[v] = -t[v];
-            dflux<EQ, 1>(rf, oB, A.ph, t);
-#pragma unroll
-            for (int v = 0; v < V; ++v) sB[v] = -t[v];
-        } else {
-#pragma unroll
-            for (int v = 0; v < V; ++v) sL[v] = sB[v] = oL[v] = oB[v] = T(0);
+                for (int v = 0; v < V; ++v) ryS[L::sq(v, el, b, k)] = ry[b][v];
         }
     }
     __syncthreads();
 
-    // ---- phase 3: common flux on the own left and lower faces --------------
-    // (and on the right / upper face of the tile's last column / row), all
-    // relative to the own reference; the value for the left / lower
-    // neighbour is shifted to that neighbour's reference.
-    T JL[V], JB[V], JR[V], JT[V];
+    // ---- phase 3: common fluxes and jumps ----------------------------------
+    // Each element takes the face points of its left and lower faces (the
+    // tile's right and upper edges go to dedicated threads), evaluates the
+    // common flux once relative to its own reference, and forms the jumps
+    // F* - f of both elements of the face: its own (kept) and the
+    // neighbour's (over the neighbour's edge flux in shared memory, shifted to
+    // the neighbour's reference).
+    T JL[V];
     if (valid) {
-        T dm[V], G[V];
+        if constexpr (!L::RYSEP) {
 #pragma unroll
-        for (int v = 0; v < V; ++v) dm[v] = lwall ? eL[v] : xR[L::xr(v, ty, tx, k)] + oL[v];
+            for (int b = 0; b < N; ++b)
+#pragma unroll
+                for (int v = 0; v < V; ++v) ryS[L::sq(v, el, b, k)] = ry[b][v];
+        }
+        T q0[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) q0[v] = DELTA ? rfS[L::rf(v, tx, ty)] : T(0);
+        if constexpr (DELTA) rf = make_ref<EQ>(q0, A.ph);
+        T o[V], dm[V], G[V], sh[V];
+        // left face
+#pragma unroll
+        for (int v = 0; v < V; ++v) o[v] = (DELTA && !lwall) ? rfS[L::rf(v, tx - 1, ty)] - q0[v] : T(0);
+#pragma unroll
+        for (int v = 0; v < V; ++v) dm[v] = lwall ? eL[v] : xR[L::xr(v, ty, tx, k)] + o[v];
         face_flux<EQ, FLUX, 0, DELTA>(rf, dm, eL, A.ph, G);
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            JL[v] = G[v] - fL[v];
-            if (tx > 0) xG[L::xg(v, ty, tx, k)] = G[v] + sL[v];
-        }
+        for (int v = 0; v < V; ++v) JL[v] = G[v] - fL[v];
+        if (tx > 0) {
+            // f(ref_own) - f(ref_left) = -(f(ref_own + (ref_left - ref_own)) - f(ref_own))
+            if constexpr (DELTA) dflux<EQ, 0>(rf, o, A.ph, sh);
 #pragma unroll
-        for (int v = 0; v < V; ++v) dm[v] = bwall ? eB[v] : yT[L::yt(v, ty, tx, k)] + oB[v];
+            for (int v = 0; v < V; ++v) {
+                T* pj = xF + L::ef(v, el - 1, k);
+                *pj = (DELTA ? G[v] - sh[v] : G[v]) - *pj;
+            }
+        }
+        // lower face
+#pragma unroll
+        for (int v = 0; v < V; ++v) o[v] = (DELTA && !bwall) ? rfS[L::rf(v, tx, ty - 1)] - q0[v] : T(0);
+#pragma unroll
+        for (int v = 0; v < V; ++v) dm[v] = bwall ? eB[v] : yT[L::yt(v, ty, tx, k)] + o[v];
         face_flux<EQ, FLUX, 1, DELTA>(rf, dm, eB, A.ph, G);
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            JB[v] = G[v] - gB[v];
-            if (ty > 0) yG[L::yg(v, ty, tx, k)] = G[v] + sB[v];
-        }
-        if (redge) {
-            T dp[V], eR[V];
+        for (int v = 0; v < V; ++v) jB[L::ef(v, el, k)] = G[v] - gB[v];
+        if (ty > 0) {
+            if constexpr (DELTA) dflux<EQ, 1>(rf, o, A.ph, sh);
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                eR[v] = xR[L::xr(v, ty, tx + 1, k)];
-                dp[v] = rwall ? eR[v] : xH[L::xh(v, ty, k)] + (DELTA ? rfS[L::rf(v, tx + 1, ty)] - rf.q[v] : T(0));
+                T* pj = yF + L::ef(v, el - TX, k);
+                *pj = (DELTA ? G[v] - sh[v] : G[v]) - *pj;
             }
-            face_flux<EQ, FLUX, 0, DELTA>(rf, eR, dp, A.ph, G);
-#pragma unroll
-            for (int v = 0; v < V; ++v) JR[v] = G[v] - fR[v];
         }
-        if (tedge) {
-            T dp[V], eT[V];
+    }
+    if (tid < (TX + TY) * N) {
+        // right face of the tile's last column (x) / upper face of its last row
+        const bool xe = tid < TY * N;
+        const int r = xe ? tid : tid - TY * N;
+        const int pos = r / N, kk = r % N;
+        if (pos < (xe ? TYe : TXe)) {
+            const int ex = xe ? TXe - 1 : pos, ey = xe ? pos : TYe - 1;
+            const bool wall = xe ? (A.bcx && i0 + TXe == A.nx) : (A.bcy && j0 + TYe == A.ny);
+            T qe[V], Em[V], dp[V], G[V];
+            Ref<T> re;
+#pragma unroll
+            for (int v = 0; v < V; ++v) qe[v] = DELTA ? rfS[L::rf(v, ex, ey)] : T(0);
+            if constexpr (DELTA) re = make_ref<EQ>(qe, A.ph);
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                eT[v] = yT[L::yt(v, ty + 1, tx, k)];
-                dp[v] = twall ? eT[v] : yH[L::yh(v, tx, k)] + (DELTA ? rfS[L::rf(v, tx, ty + 1)] - rf.q[v] : T(0));
+                Em[v] = xe ? xR[L::xr(v, ey, ex + 1, kk)] : yT[L::yt(v, ey + 1, ex, kk)];
+                if (wall) {
+                    dp[v] = Em[v];
+                } else {
+                    const T h = xe ? xH[L::xh(v, ey, kk)] : yH[L::yh(v, ex, kk)];
+                    const T on = DELTA ? (xe ? rfS[L::rf(v, ex + 1, ey)] : rfS[L::rf(v, ex, ey + 1)]) - qe[v] : T(0);
+                    dp[v] = h + on;
+                }
             }
-            face_flux<EQ, FLUX, 1, DELTA>(rf, eT, dp, A.ph, G);
+            if (xe) face_flux<EQ, FLUX, 0, DELTA>(re, Em, dp, A.ph, G);
+            else face_flux<EQ, FLUX, 1, DELTA>(re, Em, dp, A.ph, G);
+            T* J = xe ? xF : yF;
 #pragma unroll
-            for (int v = 0; v < V; ++v) JT[v] = G[v] - gT[v];
+            for (int v = 0; v < V; ++v) {
+                T* pj = J + L::ef(v, ey * TX + ex, kk);
+                *pj = G[v] - *pj;
+            }
         }
     }
     __syncthreads();
 
-    // ---- phase 4: y-part of R into the accumulator ------------------------
-    if (valid) {
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            if (!redge) JR[v] = xG[L::xg(v, ty, tx + 1, k)] - fR[v];
-            if (!tedge) JT[v] = yG[L::yg(v, ty + 1, tx, k)] - gT[v];
-#pragma unroll
-            for (int b = 0; b < N; ++b) {
-                T ys = ry[b][v] + JB[v] * tb.dgl[b];
-                ys = ys + JT[v] * tb.dgr[b];
-                rS[L::sq(v, el, b * N + k)] = -A.rhy2 * ys;
-            }
-        }
-    }
-    __syncthreads();
-
-    // ---- phase 5: x-part of R, stage update, store --------------------------
+    // ---- phase 4: R on row k, stage update, store ----------------------------
     T o[N][V];
     if (valid) {
+        // g_L'(eta_k), g_R'(eta_k): one select chain instead of an indexed
+        // parameter load
+        T glk = tb.dgl[0], grk = tb.dgr[0];
+#pragma unroll
+        for (int b = 1; b < N; ++b) {
+            if (k == b) {
+                glk = tb.dgl[b];
+                grk = tb.dgr[b];
+            }
+        }
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            T acc[N];
-            sm_load_row<N>(rS + L::sq(v, el, k * N), acc);
+            T acc[N], jb[N], jt[N];
+            sm_load_row<N>(ryS + L::sq(v, el, k, 0), acc);
+            sm_load_row<N>(jB + L::ef(v, el, 0), jb);
+            sm_load_row<N>(yF + L::ef(v, el, 0), jt);
+            const T JR = xF[L::ef(v, el, k)];
 #pragma unroll
             for (int a = 0; a < N; ++a) {
+                T ys = acc[a] + jb[a] * glk;
+                ys = ys + jt[a] * grk;
                 T xs = rx[a][v] + JL[v] * tb.dgl[a];
-                xs = xs + JR[v] * tb.dgr[a];
-                o[a][v] = acc[a] - A.rhx2 * xs;
+                xs = xs + JR * tb.dgr[a];
+                o[a][v] = -A.rhy2 * ys - A.rhx2 * xs;
             }
         }
         const long long off = e * NN + k * N;

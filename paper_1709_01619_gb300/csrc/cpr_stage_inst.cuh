@@ -16,8 +16,8 @@ static cudaError_t stage_one(const LaunchCfg& c, const StageArgs<T>& A, int ctas
 {
     constexpr int N = P + 1, V = NVars<EQ>::value;
     constexpr int NT = kTileX * kTileY * N;
-    const size_t smem = sizeof(T) * StageLayout<N, V, kTileX, kTileY>::TOTAL;
-    auto kern = cpr_stage_kernel<T, P, EQ, DIV, FLUX, kTileX, kTileY, sizeof(T) == 4>;
+    const size_t smem = sizeof(T) * StageLayout<N, V, kTileX, kTileY, stage_delta<T>()>::TOTAL;
+    auto kern = cpr_stage_kernel<T, P, EQ, DIV, FLUX, kTileX, kTileY, stage_delta<T>()>;
     if (prep) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     kern<<<ctas, NT, smem, s>>>(A);
     return cudaGetLastError();
