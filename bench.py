@@ -50,6 +50,11 @@ HBM_NX, HBM_STEPS = 1024, 20
 # per step (53.3 B per DOF-stage); both are reported.
 ALGO_ARRAYS_PER_STEP = 8
 MOVED_ARRAYS_PER_STEP = 10
+# DRAM bytes (read + write) per stage launch, mean over the three RK stages,
+# from ncu captures of the stage kernel as it stands (profiles/): the
+# 128^2 workload replayed cold (writes stay in L2) and the 1024^2 case.
+NCU_TRAFFIC_128 = 8.438e6
+NCU_TRAFFIC_1024 = 8.580e8
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -254,7 +259,7 @@ def hbm_case(make, peak, steps=HBM_STEPS):
     movedH = achievedH * MOVED_ARRAYS_PER_STEP / ALGO_ARRAYS_PER_STEP
     ctxH.close()
     return {"workload": "euler_vortex_1024x1024_p3_fp32", "bound": "hbm", "achieved": achievedH,
-            "peak": peak, "unit": "GB/s", "frac": achievedH / peak,
+            "peak": peak, "unit": "GB/s", "frac": achievedH / peak, "traffic": NCU_TRAFFIC_1024,
             "moved_gbs": movedH, "moved_frac": movedH / peak, "launch_ms": launchH,
             "dof_stage_per_s": dofH * 3 * steps / (msH * 1e-3), "rk3_steps": steps}
 
@@ -423,9 +428,10 @@ def run_cpr(args, world, rank, local):
                    "l2_flush": "256 MiB write before every timed solve",
                    "replicas": world},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                     "frac": achieved / peak, "traffic": NCU_TRAFFIC_128, "peak_source": peak_kind,
                      "kernel": "cpr_stage_kernel<float,3,Euler,LP,Rusanov>",
-                     "note": "state (4.2 MB) is L2-resident at this size"},
+                     "bytes_per_launch": bytes_per_launch,
+                     "note": "state (4.2 MB) is L2-resident at this size; traffic from a cold ncu replay"},
         "roofline_hbm_case": hbm,
         "batch": batch,
         "f64": {"value": value64, "unit": UNIT, "ms_per_solve": ms64, "rk3_steps": n64,
