@@ -298,6 +298,108 @@ def batch_case(peak, steps=100, warmup=3):
             "tuned": [{"p": p, "family": f, "grid": g} for p, f, g in choices]}
 
 
+def limited_case(peak, fp64_steps=100):
+    """Four-quadrant Riemann problem on [0,1]^2 split at (0.8, 0.8), 512^2
+    elements, p = 2, TVB minmod limiter (M = 50, eps = 1e-3) after every RK
+    stage, transmissive boundaries, CFL 0.1: the FP32 solve to t = 0.3 timed
+    whole (the initial condition limited once, outside the timing); FP64 timed
+    over a fixed number of CFL steps."""
+    import torch
+    from paper_1709_01619_gb300 import _native as nat
+    from paper_1709_01619_gb300 import inputs
+    nx, p, t_end = 512, 2, 0.3
+
+    def make(dtype):
+        cfg = nat.Config(eqn=nat.EULER, nx=nx, ny=nx, p=p, x1=1.0, y1=1.0, bc_x=nat.TRANSMISSIVE,
+                         bc_y=nat.TRANSMISSIVE, limiter=1, tvb_M=50.0, lim_eps=1e-3, cfl=0.1, dtype=dtype)
+        ctx = nat.Context(cfg)
+        x, y = ctx.point_coords()
+        q0 = torch.tensor(inputs.four_quadrant(x, y), dtype=cfg.torch_dtype, device="cuda")
+        ctx.limit(q0)
+        return ctx, q0
+
+    dof = nx * nx * (p + 1) ** 2
+    ctx, q0 = make(nat.F32)
+    q = q0.clone()
+    ctx.set_time(0.0, 0)
+    ctx.step(q, 100000, 0.0, t_end)
+    nsteps = ctx.get_time()[1]
+    q.copy_(q0)
+    ctx.set_time(0.0, 0)
+    torch.cuda.synchronize()
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    ev[0].record()
+    ctx.step(q, nsteps, 0.0, t_end)
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    nrm = ctx.norms(q)
+    ctx.close()
+    rate = dof * 3 * nsteps / (ms * 1e-3)
+    # stage kernel (8/3 state arrays per stage) + limiter (reads the state)
+    achieved = rate * 16 * (8.0 / 3.0 + 1.0) / 1e9
+    ctx64, q64 = make(nat.F64)
+    ctx64.step(q64, 5)
+    torch.cuda.synchronize()
+    ev[0].record()
+    ctx64.step(q64, fp64_steps)
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms64 = ev[0].elapsed_time(ev[1])
+    ctx64.close()
+    return {"workload": "euler_four_quadrant_512x512_p2_tvb_limiter_t0.3", "rk3_steps": nsteps,
+            "ms_fp32": ms, "dof_stage_per_s_fp32": rate, "bound": "hbm", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak,
+            "bytes_per_dof_stage": 16 * (8.0 / 3.0 + 1.0),
+            "dof_stage_per_s_fp64": dof * 3 * fp64_steps / (ms64 * 1e-3), "fp64_steps_timed": fp64_steps,
+            "n_marked_final": nrm["n_marked"], "n_nonphys_final": nrm["n_nonphys"]}
+
+
+def adjoint_case():
+    """Gradient of J = 1/2 sum W (q_N - q_t)^2 with respect to the initial
+    state: Euler vortex (strength 5) on [0,10]^2, 256^2, p = 3, FP32, 400
+    SSP-RK3 steps of dt = 7e-4 (t = 0.28, CFL 0.07), checkpoints every 20
+    steps, q_t the forward
+    solution from strength 4.5.  Forward (with checkpoints) and backward
+    (recompute + transposed steps) timed with CUDA events."""
+    import torch
+    from paper_1709_01619_gb300 import _native as nat
+    from paper_1709_01619_gb300 import adjoint, inputs
+    n, nsteps, dt, every = 256, 400, 7e-4, 20
+    cfg = nat.Config(eqn=nat.EULER, nx=n, ny=n, p=3, x1=L, y1=L, dtype=nat.F32)
+    with nat.Context(cfg) as ctx:
+        x, y = ctx.point_coords()
+        q0 = torch.tensor(inputs.vortex(x, y, eps=EPS), dtype=torch.float32, device="cuda")
+        qt = torch.tensor(inputs.vortex(x, y, eps=4.5), dtype=torch.float32, device="cuda")
+        ctx.step(qt, nsteps, dt)
+        W = adjoint.quadrature_weights(ctx)
+
+        def grad(ev=None):
+            q = q0.clone().requires_grad_(True)
+            if ev:
+                ev[0].record()
+            qN = adjoint.rollout(q, ctx, nsteps, dt, every)
+            J = 0.5 * (W * (qN - qt) ** 2).sum()
+            if ev:
+                ev[1].record()
+            J.backward()
+            if ev:
+                ev[2].record()
+            return q.grad
+
+        grad()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        g = grad(ev)
+        torch.cuda.synchronize()
+        fwd, bwd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+        finite = bool(torch.isfinite(g).all())
+    dof = n * n * 16
+    return {"workload": "euler_vortex_256x256_p3_fp32_adjoint_400steps_ckpt20", "forward_ms": fwd,
+            "backward_ms": bwd, "gradient_ms": fwd + bwd, "backward_over_forward": bwd / fwd,
+            "forward_dof_stage_per_s": dof * 3 * nsteps / (fwd * 1e-3), "gradient_finite": finite}
+
+
 def run_hbm_only(args):
     import torch
     from paper_1709_01619_gb300 import _native as nat
@@ -410,6 +512,8 @@ def run_cpr(args, world, rank, local):
 
     hbm = hbm_case(make, peak)
     batch = batch_case(peak)
+    limited = limited_case(peak)
+    adj = adjoint_case()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, s, secs, thr = oracle_sample(12.0)
@@ -434,6 +538,8 @@ def run_cpr(args, world, rank, local):
                      "note": "state (4.2 MB) is L2-resident at this size; traffic from a cold ncu replay"},
         "roofline_hbm_case": hbm,
         "batch": batch,
+        "limited": limited,
+        "adjoint": adj,
         "f64": {"value": value64, "unit": UNIT, "ms_per_solve": ms64, "rk3_steps": n64,
                 "bound": "alu"},
         "l2_rho_avg_error": {"f32": err32, "f64": err64},

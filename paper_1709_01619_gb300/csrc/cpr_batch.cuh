@@ -47,6 +47,7 @@ struct BatchArgs {
     int mode;          // stage mode (cpr_common.cuh)
     int swap;          // increment form: the high part of q^n is in Y (else X)
     Tab<T> tab;        // operator tables of the group's order
+    TabPr<T> tp;       // the same in pairs over points
 };
 
 // Register budget: as the single-problem kernel.
@@ -103,7 +104,7 @@ __device__ __forceinline__ void batch_item(const BatchArgs<T>& B, int w, StageAr
         s_n = I.ntiles;
     }
     __syncthreads();
-    stage_tile<T, P, EQ, DIV, FLUX, TX, TY, DELTA>(sA, B.tab, s_t, threadIdx.x, smem_raw, s_t, s_n);
+    stage_tile<T, P, EQ, DIV, FLUX, TX, TY, DELTA>(sA, B.tab, B.tp, s_t, threadIdx.x, smem_raw, s_t, s_n);
 }
 
 // PERSIST: CTAs walk the work list with a grid stride; otherwise the grid

@@ -112,6 +112,7 @@ cudaError_t batch_launch(cpr_batch* b, Group& g, int fam, int grid, int mode, in
     B.mode = mode;
     B.swap = swap;
     B.tab = cpr::host_tab<T>(b->lcs[g.members[0]].tab);
+    B.tp = cpr::host_tabpr<T>(b->lcs[g.members[0]].tab);
     const LaunchCfg& lc = b->lcs[g.members[0]];
     return fam == 0 ? cpr::batch_fam<T, 0>(g.p, lc.eqn, lc.flux, B, grid, s, 0, nullptr)
                     : cpr::batch_fam<T, 1>(g.p, lc.eqn, lc.flux, B, grid, s, 0, nullptr);

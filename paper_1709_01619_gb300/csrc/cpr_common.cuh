@@ -431,4 +431,94 @@ __device__ __forceinline__ T minmod3(T a, T b, T c)
     return T(0);
 }
 
+// ---- two-lane arithmetic ----------------------------------------------------
+// Pr<T> holds one value of two solution points of a line.  In FP32 the
+// operations map onto Blackwell's packed FFMA2 / FMUL2 / FADD2 instructions
+// (two IEEE single-precision operations, each rounded as its scalar
+// counterpart, in one issue slot); in FP64 they are two scalar operations.
+template <class T>
+struct Pr;
+template <>
+struct alignas(8) Pr<float> {
+    float2 v;
+};
+template <>
+struct alignas(16) Pr<double> {
+    double2 v;
+};
+
+__device__ __forceinline__ Pr<float> pmk(float a, float b) { return {make_float2(a, b)}; }
+__device__ __forceinline__ Pr<double> pmk(double a, double b) { return {make_double2(a, b)}; }
+template <class T>
+__device__ __forceinline__ Pr<T> pbc(T a) { return pmk(a, a); }
+
+__device__ __forceinline__ Pr<float> pfma(Pr<float> a, Pr<float> b, Pr<float> c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ Pr<float> pmul(Pr<float> a, Pr<float> b) { return {__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ Pr<float> padd(Pr<float> a, Pr<float> b) { return {__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ Pr<double> pfma(Pr<double> a, Pr<double> b, Pr<double> c)
+{
+    return {make_double2(fma(a.v.x, b.v.x, c.v.x), fma(a.v.y, b.v.y, c.v.y))};
+}
+__device__ __forceinline__ Pr<double> pmul(Pr<double> a, Pr<double> b)
+{
+    return {make_double2(a.v.x * b.v.x, a.v.y * b.v.y)};
+}
+__device__ __forceinline__ Pr<double> padd(Pr<double> a, Pr<double> b)
+{
+    return {make_double2(a.v.x + b.v.x, a.v.y + b.v.y)};
+}
+// a - b, exact as b * (-1) + a
+template <class T>
+__device__ __forceinline__ Pr<T> psub(Pr<T> a, Pr<T> b) { return pfma(b, pbc(T(-1)), a); }
+template <class T>
+__device__ __forceinline__ Pr<T> prcp(Pr<T> a) { return pmk(frcp(a.v.x), frcp(a.v.y)); }
+
+// Euler flux f (DIR 0) or g (DIR 1) of Eq. 4 at two points; q, f: V pairs.
+template <int EQ, int DIR, class T>
+__device__ __forceinline__ void flux_pair(const Pr<T>* q, const Phys<T>& ph, Pr<T>* f)
+{
+    if constexpr (EQ == EQ_ADV) {
+        f[0] = pmul(pbc(DIR == 0 ? ph.ax : ph.ay), q[0]);
+    } else {
+        const Pr<T> r = prcp(q[0]);
+        const Pr<T> u = pmul(q[1], r), v = pmul(q[2], r);
+        Pr<T> t = pmul(q[1], u);
+        t = pfma(q[2], v, t);
+        const Pr<T> p = pmul(pbc(ph.gamma - T(1)), pfma(pbc(T(-0.5)), t, q[3]));
+        if constexpr (DIR == 0) {
+            f[0] = q[1];
+            f[1] = pfma(q[1], u, p);
+            f[2] = pmul(q[2], u);
+            f[3] = pmul(padd(q[3], p), u);
+        } else {
+            f[0] = q[2];
+            f[1] = pmul(q[1], v);
+            f[2] = pfma(q[2], v, p);
+            f[3] = pmul(padd(q[3], p), v);
+        }
+    }
+}
+
+// sum_l c_l x_l over a line of 2 NP values held as NP pairs: products
+// accumulated per lane, then the two lanes added.  Every edge state of the
+// stage kernel (own or neighbour's) goes through this one sequence, so the
+// two CTAs that share a face see the same bits.
+template <int NP, class T>
+__device__ __forceinline__ T pdot(const Pr<T>* c, const Pr<T>* x)
+{
+    Pr<T> s = pmul(c[0], x[0]);
+#pragma unroll
+    for (int j = 1; j < NP; ++j) s = pfma(c[j], x[j], s);
+    return s.v.x + s.v.y;
+}
+
+// Operator tables in pairs over points (even N): D2[i][l] = (D[2i][l],
+// D[2i+1][l]); lm2[j] = (lm[2j], lm[2j+1]) and likewise lp2, dgl2, dgr2.
+template <class T>
+struct TabPr {
+    Pr<T> D2[(kMaxN + 1) / 2][kMaxN];
+    Pr<T> lm2[(kMaxN + 1) / 2], lp2[(kMaxN + 1) / 2];
+    Pr<T> dgl2[(kMaxN + 1) / 2], dgr2[(kMaxN + 1) / 2];
+};
+
 }  // namespace cpr

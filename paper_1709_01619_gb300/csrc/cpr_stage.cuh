@@ -67,6 +67,7 @@ struct StageArgs {
     T rhx2, rhy2;     // 2/hx, 2/hy
     Phys<T> ph;
     Tab<T> tab;
+    TabPr<T> tp;      // the tables in pairs over points (two-lane path)
 };
 
 template <int N, int V, int TX, int TY, bool DELTA>
@@ -245,11 +246,15 @@ constexpr int stage_min_blocks()
 // in the barriers.  slot / nslots: this tile's entry in the per-CTA partial
 // maxima of the instance (the last tile to finish reduces them).
 template <class T, int P, int EQ, int DIV, int FLUX, int TX, int TY, bool DELTA>
-__device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& tb, int tile, int tid,
-                                           unsigned char* smem_raw, int slot, int nslots)
+__device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& tb, const TabPr<T>& tp, int tile,
+                                           int tid, unsigned char* smem_raw, int slot, int nslots)
 {
     constexpr int N = P + 1, NN = N * N, V = NVars<EQ>::value;
     constexpr int NT = TX * TY * N;
+    // Two-lane path (pairs of points of a line; packed FP32 instructions):
+    // even N, LP divergence, fluxes evaluated directly.
+    constexpr bool PAIRED = N % 2 == 0 && DIV == DIV_LP && !DELTA;
+    constexpr int NP = N / 2;
     static_assert(TX * TY >= TX + TY, "every tile-edge face point needs a thread of its own");
     using L = StageLayout<N, V, TX, TY, DELTA>;
     T* sq = reinterpret_cast<T*>(smem_raw);
@@ -308,6 +313,36 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
         }
         if constexpr (DELTA) rf = make_ref<EQ>(q0, A.ph);
         T f[N][V], col[N], eR[V], fR[V];
+        if constexpr (PAIRED) {
+            Pr<T> qp[NP][V], fp[NP][V];
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) qp[j][v] = pmk(d[2 * j][v], d[2 * j + 1][v]);
+                flux_pair<EQ, 0>(qp[j], A.ph, fp[j]);
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                Pr<T> cq[NP], cf[NP];
+#pragma unroll
+                for (int j = 0; j < NP; ++j) {
+                    cq[j] = qp[j][v];
+                    cf[j] = fp[j][v];
+                }
+                eL[v] = pdot<NP>(tp.lm2, cq);
+                eR[v] = pdot<NP>(tp.lp2, cq);
+                fL[v] = pdot<NP>(tp.lm2, cf);
+                fR[v] = pdot<NP>(tp.lp2, cf);
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    Pr<T> r = pmul(tp.D2[i][0], pbc(cf[0].v.x));
+#pragma unroll
+                    for (int l = 1; l < N; ++l) r = pfma(tp.D2[i][l], pbc(l % 2 ? cf[l / 2].v.y : cf[l / 2].v.x), r);
+                    rx[2 * i][v] = r.v.x;
+                    rx[2 * i + 1][v] = r.v.y;
+                }
+            }
+        } else {
 #pragma unroll
         for (int a = 0; a < N; ++a) line_flux<EQ, 0, DELTA>(rf, d[a], A.ph, f[a]);
 #pragma unroll
@@ -343,6 +378,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
             line_flux<EQ, 0, DELTA>(rf, eL, A.ph, fL);
             line_flux<EQ, 0, DELTA>(rf, eR, A.ph, fR);
         }
+        }
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             xR[L::xr(v, ty, tx + 1, k)] = eR[v];
@@ -351,7 +387,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
     }
     {
         constexpr int NXH = 2 * TY * N, NYH = 2 * TX * N;
-        for (int t = tid; active && t < NXH + NYH; t += NT) {
+        // one (line, variable) per thread and pass: all warps share the
+        // halo loads
+        for (int tv = tid; active && tv < V * (NXH + NYH); tv += NT) {
+            const int v = tv / (NXH + NYH), t = tv - v * (NXH + NYH);
             const bool xdir = t < NXH;
             const int r0 = xdir ? t : t - NXH;
             const int side = xdir ? r0 / (TY * N) : r0 / (TX * N);
@@ -378,8 +417,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
             const int lx = xdir ? (side ? TXe : -1) : pos;
             const int ly = xdir ? pos : (side ? TYe : -1);
             const T* coef = side ? tb.lm : tb.lp;  // the edge facing the tile
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
+            {
                 const T* src = A.qs + v * A.npts + eh * NN;
                 const T* srb = addb ? A.qb + v * A.npts + eh * NN : src;
                 T ref = T(0);
@@ -399,7 +437,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
                 }
 #pragma unroll
                 for (int l = 0; l < N; ++l) line[l] -= ref;
-                const T dv = line_dot<N>(coef, line);
+                T dv;
+                if constexpr (PAIRED) {
+                    Pr<T> lp2[NP];
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) lp2[j] = pmk(line[2 * j], line[2 * j + 1]);
+                    dv = pdot<NP>(side ? tp.lm2 : tp.lp2, lp2);
+                } else {
+                    dv = line_dot<N>(coef, line);
+                }
                 if (xdir) {
                     if (side) xH[L::xh(v, pos, kk)] = dv;
                     else xR[L::xr(v, pos, 0, kk)] = dv;
@@ -425,6 +471,36 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
                 const T x = sq[L::sq(v, el, b, k)];
                 d[b][v] = DELTA ? x - rf.q[v] : x;
             }
+        if constexpr (PAIRED) {
+            Pr<T> qp[NP][V], gp[NP][V];
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) qp[j][v] = pmk(d[2 * j][v], d[2 * j + 1][v]);
+                flux_pair<EQ, 1>(qp[j], A.ph, gp[j]);
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                Pr<T> cq[NP], cg[NP];
+#pragma unroll
+                for (int j = 0; j < NP; ++j) {
+                    cq[j] = qp[j][v];
+                    cg[j] = gp[j][v];
+                }
+                eB[v] = pdot<NP>(tp.lm2, cq);
+                eT[v] = pdot<NP>(tp.lp2, cq);
+                gB[v] = pdot<NP>(tp.lm2, cg);
+                gT[v] = pdot<NP>(tp.lp2, cg);
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    Pr<T> r = pmul(tp.D2[i][0], pbc(cg[0].v.x));
+#pragma unroll
+                    for (int l = 1; l < N; ++l) r = pfma(tp.D2[i][l], pbc(l % 2 ? cg[l / 2].v.y : cg[l / 2].v.x), r);
+                    ry[2 * i][v] = r.v.x;
+                    ry[2 * i + 1][v] = r.v.y;
+                }
+            }
+        } else {
 #pragma unroll
         for (int b = 0; b < N; ++b) line_flux<EQ, 1, DELTA>(rf, d[b], A.ph, g[b]);
 #pragma unroll
@@ -459,6 +535,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
             }
             line_flux<EQ, 1, DELTA>(rf, eB, A.ph, gB);
             line_flux<EQ, 1, DELTA>(rf, eT, A.ph, gT);
+        }
         }
 #pragma unroll
         for (int v = 0; v < V; ++v) {
@@ -584,6 +661,18 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
             sm_load_row<N>(jB + L::ef(v, el, 0), jb);
             sm_load_row<N>(yF + L::ef(v, el, 0), jt);
             const T JR = xF[L::ef(v, el, k)];
+            if constexpr (PAIRED) {
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    Pr<T> ys = pfma(pmk(jb[2 * i], jb[2 * i + 1]), pbc(glk), pmk(acc[2 * i], acc[2 * i + 1]));
+                    ys = pfma(pmk(jt[2 * i], jt[2 * i + 1]), pbc(grk), ys);
+                    Pr<T> xs = pfma(pbc(JL[v]), tp.dgl2[i], pmk(rx[2 * i][v], rx[2 * i + 1][v]));
+                    xs = pfma(pbc(JR), tp.dgr2[i], xs);
+                    const Pr<T> r = pfma(pbc(-A.rhx2), xs, pmul(pbc(-A.rhy2), ys));
+                    o[2 * i][v] = r.v.x;
+                    o[2 * i + 1][v] = r.v.y;
+                }
+            } else {
 #pragma unroll
             for (int a = 0; a < N; ++a) {
                 T ys = acc[a] + jb[a] * glk;
@@ -591,6 +680,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
                 T xs = rx[a][v] + JL[v] * tb.dgl[a];
                 xs = xs + JR * tb.dgr[a];
                 o[a][v] = -A.rhy2 * ys - A.rhx2 * xs;
+            }
             }
         }
         const long long off = e * NN + k * N;
@@ -691,7 +781,7 @@ __global__ void __launch_bounds__(TX * TY * (P + 1), (stage_min_blocks<T, P + 1>
 cpr_stage_kernel(const StageArgs<T> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    stage_tile<T, P, EQ, DIV, FLUX, TX, TY, DELTA>(A, A.tab, blockIdx.x, threadIdx.x, smem_raw, blockIdx.x,
+    stage_tile<T, P, EQ, DIV, FLUX, TX, TY, DELTA>(A, A.tab, A.tp, blockIdx.x, threadIdx.x, smem_raw, blockIdx.x,
                                                    gridDim.x);
 }
 

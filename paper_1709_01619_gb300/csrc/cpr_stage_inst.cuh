@@ -64,6 +64,7 @@ static StageArgs<T> make_stage_args(const LaunchCfg& c, int mode, const StagePtr
     A.ph.ax = T(c.ax);
     A.ph.ay = T(c.ay);
     A.tab = host_tab<T>(c.tab);
+    A.tp = host_tabpr<T>(c.tab);
     return A;
 }
 

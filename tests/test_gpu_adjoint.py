@@ -137,3 +137,40 @@ def test_fp32_gradient_against_oracle_adjoint_16x16():
         (0.5 * (W * (qN - dev(qt, c)) ** 2).sum()).backward()
         g = q0d.grad.double().cpu().numpy()
     assert rel(g, gbar) <= 1e-4
+
+
+def test_config5_gradient_full_size_vs_fp64_differences():
+    """Adjoint workload at full size: J = 1/2 sum W (q_N - q_t)^2 for the
+    Euler vortex (strength 5) on [0,10]^2, 256 x 256, p = 3, 400 SSP-RK3 steps
+    of dt = 7e-4 (t = 0.28, CFL 0.07 at the vortex's largest signal speed of
+    about 3.9; 400 stable steps cannot reach t = 2),
+    checkpoints every 20 steps; q_t is the forward solution from the vortex
+    of strength 4.5.  The FP32 adjoint gradient, projected on 32 random
+    directions, against central differences of J computed by the FP64 GPU
+    solver."""
+    n, nsteps, dt = 256, 400, 7e-4
+    c32 = nat.Config(dtype=nat.F32, eqn=nat.EULER, nx=n, ny=n, p=3, x1=10.0, y1=10.0)
+    c64 = nat.Config(dtype=nat.F64, eqn=nat.EULER, nx=n, ny=n, p=3, x1=10.0, y1=10.0)
+    with nat.Context(c64) as ctx64, nat.Context(c32) as ctx32:
+        x, y = ctx64.point_coords()
+        q0 = torch.tensor(inputs.vortex(x, y, eps=5.0), device="cuda")
+        qt = torch.tensor(inputs.vortex(x, y, eps=4.5), device="cuda")
+        ctx64.step(qt, nsteps, dt)
+        W64 = adjoint.quadrature_weights(ctx64)
+
+        def J64(q):
+            q = q.clone()
+            ctx64.step(q, nsteps, dt)
+            return float(0.5 * (W64 * (q - qt) ** 2).sum())
+
+        q32 = q0.float().requires_grad_(True)
+        qN = adjoint.rollout(q32, ctx32, nsteps, dt, every=20)
+        W32 = adjoint.quadrature_weights(ctx32)
+        (0.5 * (W32 * (qN - qt.float()) ** 2).sum()).backward()
+        g = q32.grad.double()
+        rng = np.random.default_rng(5)
+        h = 1e-4
+        for _ in range(32):
+            d = torch.tensor(rng.standard_normal(c64.shape), device="cuda")
+            fd = (J64(q0 + h * d) - J64(q0 - h * d)) / (2 * h)
+            assert float((g * d).sum()) == pytest.approx(fd, rel=2e-3)
