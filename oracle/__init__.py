@@ -30,6 +30,7 @@ GAUSS, LOBATTO = 0, 1
 DIV_LP, DIV_CHAIN = 0, 1
 RUSANOV, UPWIND = 0, 1
 PERIODIC, TRANSMISSIVE = 0, 1
+CPR, FV_MUSCL = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -60,6 +61,7 @@ class _Cfg(ctypes.Structure):
         ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
         ("limiter", ctypes.c_int), ("tvb_M", ctypes.c_double),
         ("lim_eps", ctypes.c_double), ("cfl", ctypes.c_double),
+        ("scheme", ctypes.c_int),
     ]
 
 
@@ -156,6 +158,7 @@ class Config:
     tvb_M: float = 0.0
     lim_eps: float = 1e-3
     cfl: float = 0.1
+    scheme: int = CPR  # FV_MUSCL: one average per element, p = 0
 
     @property
     def nvars(self) -> int:

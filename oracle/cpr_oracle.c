@@ -210,6 +210,15 @@ static int check_cfg(const oracle_cfg* c)
 {
     if (!c) return -1;
     if (c->eqn != OR_ADVECTION && c->eqn != OR_EULER) return -1;
+    if (c->scheme != OR_CPR && c->scheme != OR_FV_MUSCL) return -1;
+    if (c->scheme == OR_FV_MUSCL) {
+        /* one average per element; the MUSCL limiter is part of the
+         * reconstruction */
+        if (c->nx < 1 || c->ny < 1 || c->p != 0 || c->limiter) return -1;
+        if (!(c->x1 > c->x0) || !(c->y1 > c->y0)) return -1;
+        if (c->flux == OR_UPWIND && c->eqn != OR_ADVECTION) return -1;
+        return 0;
+    }
     if (c->nx < 1 || c->ny < 1 || c->p < 1 || c->p > ORACLE_PMAX) return -1;
     if (!(c->x1 > c->x0) || !(c->y1 > c->y0)) return -1;
     if (c->div == OR_DIV_CHAIN && c->eqn != OR_EULER && c->eqn != OR_ADVECTION) return -1;
@@ -220,6 +229,16 @@ static int check_cfg(const oracle_cfg* c)
 int oracle_point_coords(const oracle_cfg* c, double* x, double* y)
 {
     if (check_cfg(c)) return -1;
+    if (c->scheme == OR_FV_MUSCL) {
+        /* FV: the element centre stands for the element */
+        double hx = (c->x1 - c->x0) / c->nx, hy = (c->y1 - c->y0) / c->ny;
+        for (int j = 0; j < c->ny; ++j)
+            for (int i = 0; i < c->nx; ++i) {
+                x[(long)j * c->nx + i] = c->x0 + hx * (i + 0.5);
+                y[(long)j * c->nx + i] = c->y0 + hy * (j + 0.5);
+            }
+        return 0;
+    }
     oracle_tab T;
     oracle_tables(c->p, c->pts, &T);
     int n = T.n;
@@ -642,9 +661,80 @@ static void element_residual(const oracle_cfg* c, const oracle_tab* T, const dou
         }
 }
 
+/* ------------------------------------------------------------------------ */
+/* FV with second-order MUSCL reconstruction (Sec. 2.1; Sec. 2.6; the        */
+/* reconstruct-then-Riemann-flux steps of Algorithm 1)                       */
+/* ------------------------------------------------------------------------ */
+
+/* Average of variable v in element (i, j), ghosts included: periodic
+ * directions wrap, transmissive ones repeat the boundary element (zero
+ * gradient, so the boundary face sees the boundary state on both sides). */
+static double fv_cell(const oracle_cfg* c, const double* q, int v, int i, int j)
+{
+    int nx = c->nx, ny = c->ny;
+    if (i < 0 || i >= nx) {
+        if (c->bc_x == OR_PERIODIC) i = ((i % nx) + nx) % nx;
+        else i = i < 0 ? 0 : nx - 1;
+    }
+    if (j < 0 || j >= ny) {
+        if (c->bc_y == OR_PERIODIC) j = ((j % ny) + ny) % ny;
+        else j = j < 0 ? 0 : ny - 1;
+    }
+    return q[(long)v * nx * ny + (long)j * nx + i];
+}
+
+static double minmod2(double a, double b);
+
+/* Limited change of variable v across element (i, j) in direction d (0: x,
+ * 1: y): minmod of the forward and backward differences of the averages. */
+static double fv_slope(const oracle_cfg* c, const double* q, int v, int i, int j, int d)
+{
+    int di = d == 0, dj = d == 1;
+    double qc = fv_cell(c, q, v, i, j);
+    double fwd = fv_cell(c, q, v, i + di, j + dj) - qc;
+    double bwd = qc - fv_cell(c, q, v, i - di, j - dj);
+    return minmod2(fwd, bwd);
+}
+
+/* States on both sides of the face between element (i, j) and its +d
+ * neighbour: each element's average moved half its limited change towards
+ * the face. */
+static void fv_face_states(const oracle_cfg* c, const double* q, int i, int j, int d,
+                           double* qm, double* qp)
+{
+    int V = oracle_nvars(c), di = d == 0, dj = d == 1;
+    for (int v = 0; v < V; ++v) {
+        qm[v] = fv_cell(c, q, v, i, j) + 0.5 * fv_slope(c, q, v, i, j, d);
+        qp[v] = fv_cell(c, q, v, i + di, j + dj) - 0.5 * fv_slope(c, q, v, i + di, j + dj, d);
+    }
+}
+
+static void fv_element_residual(const oracle_cfg* c, const double* q, int i, int j, double* R)
+{
+    int V = oracle_nvars(c);
+    long ne = (long)c->nx * c->ny, e = (long)j * c->nx + i;
+    double hx = (c->x1 - c->x0) / c->nx, hy = (c->y1 - c->y0) / c->ny;
+    double qm[4], qp[4], fw[4], fe[4], gs[4], gn[4];
+    fv_face_states(c, q, i - 1, j, 0, qm, qp);
+    oracle_common_flux(c, qm, qp, 1.0, 0.0, fw);   /* f_{i-1/2,j} */
+    fv_face_states(c, q, i, j, 0, qm, qp);
+    oracle_common_flux(c, qm, qp, 1.0, 0.0, fe);   /* f_{i+1/2,j} */
+    fv_face_states(c, q, i, j - 1, 1, qm, qp);
+    oracle_common_flux(c, qm, qp, 0.0, 1.0, gs);   /* g_{i,j-1/2} */
+    fv_face_states(c, q, i, j, 1, qm, qp);
+    oracle_common_flux(c, qm, qp, 0.0, 1.0, gn);   /* g_{i,j+1/2} */
+    for (int v = 0; v < V; ++v) R[(long)v * ne + e] = -(fe[v] - fw[v]) / hx - (gn[v] - gs[v]) / hy;
+}
+
 int oracle_residual(const oracle_cfg* c, const double* q, double* R)
 {
     if (check_cfg(c) || !q || !R) return -1;
+    if (c->scheme == OR_FV_MUSCL) {
+        long ne = (long)c->nx * c->ny;
+#pragma omp parallel for schedule(static)
+        for (long e = 0; e < ne; ++e) fv_element_residual(c, q, (int)(e % c->nx), (int)(e / c->nx), R);
+        return 0;
+    }
     oracle_tab T;
     oracle_tables(c->p, c->pts, &T);
     long ne = (long)c->nx * c->ny;
@@ -743,7 +833,7 @@ static void element_residual_jvp(const oracle_cfg* c, const oracle_tab* T, const
 
 int oracle_residual_jvp(const oracle_cfg* c, const double* q, const double* dq, double* dR)
 {
-    if (check_cfg(c) || c->div != OR_DIV_LP || !q || !dq || !dR) return -1;
+    if (check_cfg(c) || c->scheme != OR_CPR || c->div != OR_DIV_LP || !q || !dq || !dR) return -1;
     oracle_tab T;
     oracle_tables(c->p, c->pts, &T);
     long ne = (long)c->nx * c->ny;
@@ -871,7 +961,7 @@ static void element_residual_vjp(const oracle_cfg* c, const oracle_tab* T, const
 
 int oracle_residual_vjp(const oracle_cfg* c, const double* q, const double* rbar, double* qbar)
 {
-    if (check_cfg(c) || c->div != OR_DIV_LP || !q || !rbar || !qbar) return -1;
+    if (check_cfg(c) || c->scheme != OR_CPR || c->div != OR_DIV_LP || !q || !rbar || !qbar) return -1;
     oracle_tab T;
     oracle_tables(c->p, c->pts, &T);
     long N = oracle_state_size(c);
@@ -889,6 +979,11 @@ int oracle_residual_vjp(const oracle_cfg* c, const double* q, const double* rbar
 int oracle_averages(const oracle_cfg* c, const double* q, double* avg)
 {
     if (check_cfg(c) || !q || !avg) return -1;
+    if (c->scheme == OR_FV_MUSCL) {
+        /* FV stores the averages themselves */
+        memcpy(avg, q, sizeof(double) * oracle_nvars(c) * c->nx * c->ny);
+        return 0;
+    }
     oracle_tab T;
     oracle_tables(c->p, c->pts, &T);
     int n = T.n, V = oracle_nvars(c);
@@ -930,7 +1025,7 @@ static double minmod_tvb(double a, double b, double c, double M, double h)
 
 long oracle_limit(const oracle_cfg* c, double* q, int* marks, double* margin)
 {
-    if (check_cfg(c) || !q) return -1;
+    if (check_cfg(c) || c->scheme != OR_CPR || !q) return -1;
     oracle_tab T;
     oracle_tables(c->p, c->pts, &T);
     int n = T.n, V = oracle_nvars(c);
@@ -1098,7 +1193,7 @@ long oracle_run(const oracle_cfg* c, double* q, long nsteps, double dt, double t
 int oracle_rk3_vjp(const oracle_cfg* c, const double* q, double dt, const double* qbar_out,
                    double* qbar_in)
 {
-    if (check_cfg(c) || c->div != OR_DIV_LP || !q || !qbar_out || !qbar_in) return -1;
+    if (check_cfg(c) || c->scheme != OR_CPR || c->div != OR_DIV_LP || !q || !qbar_out || !qbar_in) return -1;
     long N = oracle_state_size(c);
     double* R = (double*)malloc(sizeof(double) * N);
     double* q1 = (double*)malloc(sizeof(double) * N);

@@ -37,6 +37,7 @@ enum { OR_GAUSS = 0, OR_LOBATTO = 1 };
 enum { OR_DIV_LP = 0, OR_DIV_CHAIN = 1 };
 enum { OR_RUSANOV = 0, OR_UPWIND = 1 };
 enum { OR_PERIODIC = 0, OR_TRANSMISSIVE = 1 };
+enum { OR_CPR = 0, OR_FV_MUSCL = 1 };
 
 typedef struct {
     int eqn;                 /* OR_ADVECTION or OR_EULER                     */
@@ -54,6 +55,9 @@ typedef struct {
     double tvb_M;            /* TVB constant M (0: plain minmod)              */
     double lim_eps;          /* marking threshold epsilon (Sec. 2.6)          */
     double cfl;              /* CFL number for oracle_dt                      */
+    int scheme;              /* OR_CPR, or OR_FV_MUSCL: one average per       */
+                             /* element (p = 0), second-order MUSCL with      */
+                             /* minmod slopes (Sec. 2.1, 2.6, Algorithm 1)    */
 } oracle_cfg;
 
 /* 1D operator tables for n = p + 1 points. */
@@ -92,7 +96,14 @@ void oracle_common_flux(const oracle_cfg* c, const double* qm, const double* qp,
 
 /* CPR semi-discrete right-hand side R(q) = dq/dt (Sec. 2.2, Eq. 16).
  * Pinned by: equality with an independent modal DG for linear advection,
- * order p+1 convergence, freestream preservation, conservation. */
+ * order p+1 convergence, freestream preservation, conservation.
+ * scheme == OR_FV_MUSCL: the FV semi-discretisation of Sec. 2.1,
+ * dq_ij/dt = -(f_{i+1/2,j} - f_{i-1/2,j})/dx - (g_{i,j+1/2} - g_{i,j-1/2})/dy,
+ * with face states reconstructed by second-order MUSCL with minmod-limited
+ * slopes (Sec. 2.6) and the common flux of oracle_common_flux.  Pinned by:
+ * freestream, conservation, exactness on linear data, reduction to
+ * first-order upwind when every slope is limited to zero, total variation
+ * diminishing in 1D, second-order convergence, x-y symmetry. */
 int oracle_residual(const oracle_cfg* c, const double* q, double* R);
 
 /* Element averages, Algorithm 9: avg[v][e] = sum_l (w_a w_b / 4) q[v][e][l]. */
