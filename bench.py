@@ -355,6 +355,59 @@ def limited_case(peak, fp64_steps=100):
             "n_marked_final": nrm["n_marked"], "n_nonphys_final": nrm["n_nonphys"]}
 
 
+def fv_case(peak, fp64_steps=200):
+    """The FV run of the equal-DOF comparison: the same four-quadrant problem
+    on 1536^2 elements (2,359,296 DOF, as the 512^2 p = 2 CPR run), FV with
+    second-order MUSCL and minmod slopes, transmissive, CFL 0.4 (the paper's
+    FV CFL), FP32 to t = 0.3 timed whole; FP64 timed over fixed CFL steps."""
+    import torch
+    from paper_1709_01619_gb300 import _native as nat
+    from paper_1709_01619_gb300 import inputs
+    n, t_end = 1536, 0.3
+
+    def make(dtype):
+        cfg = nat.Config(eqn=nat.EULER, nx=n, ny=n, p=0, x1=1.0, y1=1.0, bc_x=nat.TRANSMISSIVE,
+                         bc_y=nat.TRANSMISSIVE, cfl=0.4, dtype=dtype, scheme=nat.SCHEME_FV_MUSCL)
+        ctx = nat.Context(cfg)
+        x, y = ctx.point_coords()
+        return ctx, torch.tensor(inputs.four_quadrant(x, y), dtype=cfg.torch_dtype, device="cuda")
+
+    ctx, q0 = make(nat.F32)
+    q = q0.clone()
+    ctx.set_time(0.0, 0)
+    ctx.step(q, 100000, 0.0, t_end)
+    nsteps = ctx.get_time()[1]
+    q.copy_(q0)
+    ctx.set_time(0.0, 0)
+    torch.cuda.synchronize()
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    ev[0].record()
+    ctx.step(q, nsteps, 0.0, t_end)
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    nrm = ctx.norms(q)
+    ctx.close()
+    dof = n * n
+    rate = dof * 3 * nsteps / (ms * 1e-3)
+    achieved = rate * 16 * ALGO_ARRAYS_PER_STEP / 3.0 / 1e9
+    ctx64, q64 = make(nat.F64)
+    ctx64.step(q64, 5)
+    torch.cuda.synchronize()
+    ev[0].record()
+    ctx64.step(q64, fp64_steps)
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms64 = ev[0].elapsed_time(ev[1])
+    ctx64.close()
+    return {"workload": "euler_four_quadrant_fv_muscl_1536x1536_t0.3", "dof": dof, "rk3_steps": nsteps,
+            "ms_fp32": ms, "dof_stage_per_s_fp32": rate, "bound": "hbm", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak,
+            "note": "state 37.7 MB per array: largely L2-resident",
+            "dof_stage_per_s_fp64": dof * 3 * fp64_steps / (ms64 * 1e-3), "fp64_steps_timed": fp64_steps,
+            "n_nonphys_final": nrm["n_nonphys"]}
+
+
 def adjoint_case():
     """Gradient of J = 1/2 sum W (q_N - q_t)^2 with respect to the initial
     state: Euler vortex (strength 5) on [0,10]^2, 256^2, p = 3, FP32, 400
@@ -513,6 +566,8 @@ def run_cpr(args, world, rank, local):
     hbm = hbm_case(make, peak)
     batch = batch_case(peak)
     limited = limited_case(peak)
+    fv = fv_case(peak)
+    fv["cpr_512_p2_over_fv_time_to_solution"] = limited["ms_fp32"] / fv["ms_fp32"]
     adj = adjoint_case()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -539,6 +594,7 @@ def run_cpr(args, world, rank, local):
         "roofline_hbm_case": hbm,
         "batch": batch,
         "limited": limited,
+        "fv_equal_dof": fv,
         "adjoint": adj,
         "f64": {"value": value64, "unit": UNIT, "ms_per_solve": ms64, "rk3_steps": n64,
                 "bound": "alu"},

@@ -62,6 +62,7 @@ enum { CPR_FLUX_RUSANOV = 0, CPR_FLUX_UPWIND = 1, CPR_FLUX_ROE = 2 }; /* .flux  
 enum { CPR_DIV_LP = 0, CPR_DIV_CHAIN = 1 };                      /* .div            */
 enum { CPR_BC_PERIODIC = 0, CPR_BC_TRANSMISSIVE = 1 };           /* .bc_x, .bc_y    */
 enum { CPR_F64 = 0, CPR_F32 = 1 };                               /* .dtype          */
+enum { CPR_SCHEME_CPR = 0, CPR_SCHEME_FV_MUSCL = 1 };            /* .scheme         */
 
 /* Problem and scheme description.
  *   eqn      CPR_ADVECTION (u_t + ax u_x + ay u_y = 0) or CPR_EULER (Sec. 2).
@@ -83,7 +84,16 @@ enum { CPR_F64 = 0, CPR_F32 = 1 };                               /* .dtype      
  *   dtype    arithmetic and storage type of the state: CPR_F64 or CPR_F32.
  *            Reductions and simulated time are FP64 in both.
  *   cfl      CFL number of the time step dt = cfl * min(hx, hy) / max_speed
- *            (Sec. 4, Eq. 36), max_speed = max over points of |u| + c. */
+ *            (Sec. 4, Eq. 36), max_speed = max over points of |u| + c.
+ *   scheme   CPR_SCHEME_CPR, or CPR_SCHEME_FV_MUSCL: the finite-volume
+ *            comparison scheme of the paper (Sec. 2.1), one average per
+ *            element, face states by second-order MUSCL reconstruction with
+ *            minmod-limited slopes (Sec. 2.6, Algorithm 1), the same common
+ *            flux, boundary conditions, time stepping and CFL rule.  FV needs
+ *            p = 0 and limiter = 0 (pts, corr and div are ignored); its state
+ *            is q[v][e] (one value per element, the element centre stands
+ *            for the element in cpr_point_coords); cpr_limit, the adjoint
+ *            entry points and batches return CPR_EINVAL for it. */
 typedef struct {
     int eqn;
     int nx, ny;
@@ -99,6 +109,7 @@ typedef struct {
     double tvb_M, lim_eps;
     int dtype;
     double cfl;
+    int scheme;
 } cpr_config;
 
 /* Results of cpr_norms (all FP64).

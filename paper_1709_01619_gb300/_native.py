@@ -24,6 +24,7 @@ RUSANOV, UPWIND, ROE = 0, 1, 2
 DIV_LP, DIV_CHAIN = 0, 1
 PERIODIC, TRANSMISSIVE = 0, 1
 F64, F32 = 0, 1
+SCHEME_CPR, SCHEME_FV_MUSCL = 0, 1
 
 _STATUS = {0: "CPR_OK", 1: "CPR_EINVAL", 2: "CPR_ENOMEM", 3: "CPR_ECUDA", 4: "CPR_ENONPHYS",
            5: "CPR_ETIMEOUT", 6: "CPR_ENOTIMPL"}
@@ -53,7 +54,7 @@ class _Config(ctypes.Structure):
         ("ax", ctypes.c_double), ("ay", ctypes.c_double), ("gamma", ctypes.c_double),
         ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int), ("limiter", ctypes.c_int),
         ("tvb_M", ctypes.c_double), ("lim_eps", ctypes.c_double), ("dtype", ctypes.c_int),
-        ("cfl", ctypes.c_double),
+        ("cfl", ctypes.c_double), ("scheme", ctypes.c_int),
     ]
 
 
@@ -91,6 +92,7 @@ class Config:
     lim_eps: float = 1e-3
     dtype: int = F64
     cfl: float = 0.1
+    scheme: int = 0  # SCHEME_CPR, or SCHEME_FV_MUSCL (p = 0: one average per element)
 
     @property
     def nvars(self) -> int:

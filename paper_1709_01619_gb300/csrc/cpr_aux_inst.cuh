@@ -50,6 +50,8 @@ static AuxArgs<T> make_aux(const LaunchCfg& c)
     do {                                                                                         \
         const bool euler = c.eqn == EQ_EULER;                                                    \
         switch (c.p) {                                                                           \
+        case 0: if (euler) KERNEL<T, 0, EQ_EULER><<<GRID, BLOCK, 0, STREAM>>>(ARGS);             \
+                else KERNEL<T, 0, EQ_ADV><<<GRID, BLOCK, 0, STREAM>>>(ARGS); break;              \
         case 1: if (euler) KERNEL<T, 1, EQ_EULER><<<GRID, BLOCK, 0, STREAM>>>(ARGS);             \
                 else KERNEL<T, 1, EQ_ADV><<<GRID, BLOCK, 0, STREAM>>>(ARGS); break;              \
         case 2: if (euler) KERNEL<T, 2, EQ_EULER><<<GRID, BLOCK, 0, STREAM>>>(ARGS);             \
@@ -66,6 +68,7 @@ template <class T>
 cudaError_t launch_stage(const LaunchCfg& c, int mode, const StagePtrs& b, bool do_wave, cudaStream_t s)
 {
     switch (c.p) {
+    case 0: return launch_fv<T>(c, mode, b, do_wave, s);
     case 1: return launch_stage_p<T, 1>(c, mode, b, do_wave, s);
     case 2: return launch_stage_p<T, 2>(c, mode, b, do_wave, s);
     case 3: return launch_stage_p<T, 3>(c, mode, b, do_wave, s);
@@ -98,6 +101,7 @@ template <class T>
 cudaError_t prepare_stage(const LaunchCfg& c)
 {
     switch (c.p) {
+    case 0: return cudaSuccess;  // the FV kernel uses static shared memory only
     case 1: return prepare_stage_p<T, 1>(c);
     case 2: return prepare_stage_p<T, 2>(c);
     case 3: return prepare_stage_p<T, 3>(c);

@@ -291,8 +291,9 @@ extern "C" cpr_status cpr_batch_init(const cpr_config* cfgs, int n, void* stream
             g_batch_init_err = "all instances need the same eqn, dtype and flux";
             return CPR_EINVAL;
         }
-        if (c.div != CPR_DIV_LP || c.pts != CPR_PTS_GAUSS || c.limiter || c.flux == CPR_FLUX_ROE) {
-            g_batch_init_err = "batches run Gauss points, LP divergence, no limiter, Rusanov or upwind flux";
+        if (c.scheme != CPR_SCHEME_CPR || c.div != CPR_DIV_LP || c.pts != CPR_PTS_GAUSS || c.limiter ||
+            c.flux == CPR_FLUX_ROE) {
+            g_batch_init_err = "batches run CPR with Gauss points, LP divergence, no limiter, Rusanov or upwind flux";
             return CPR_EINVAL;
         }
     }

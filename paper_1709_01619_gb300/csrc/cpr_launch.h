@@ -72,6 +72,10 @@ cudaError_t launch_stage_p(const LaunchCfg& c, int mode, const StagePtrs& b, boo
 template <class T, int P>
 cudaError_t prepare_stage_p(const LaunchCfg& c);
 
+// FV stage kernel (p = 0; cpr_fv.cuh), same modes and buffers as the CPR one.
+template <class T>
+cudaError_t launch_fv(const LaunchCfg& c, int mode, const StagePtrs& b, bool do_wave, cudaStream_t s);
+
 template <class T>
 cudaError_t launch_stage(const LaunchCfg& c, int mode, const StagePtrs& b, bool do_wave, cudaStream_t s);
 // Shu-Osher / residual form: modes 0..3.

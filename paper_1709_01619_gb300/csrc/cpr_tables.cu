@@ -101,6 +101,15 @@ void lobatto(int n, double* x, double* w)
 
 int build_tables(int p, int pts, HostTab* t)
 {
+    if (p == 0 && t) {
+        // the one-point element of the FV scheme: the average itself at the
+        // centre (weight 2 on [-1, 1]); no derivative, no correction
+        *t = HostTab{};
+        t->n = 1;
+        t->w[0] = 2.0;
+        t->lm[0] = t->lp[0] = 1.0;
+        return 0;
+    }
     if (p < 1 || p > kMaxN - 1 || !t) return -1;
     const int n = p + 1;
     *t = HostTab{};

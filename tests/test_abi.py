@@ -66,6 +66,9 @@ BAD = [
     dict(corr=1), dict(flux=9), dict(div=3), dict(bc_x=4), dict(gamma=1.0), dict(limiter=2),
     dict(tvb_M=-1.0), dict(lim_eps=-1.0), dict(dtype=5), dict(cfl=-0.1),
     dict(eqn=1, flux=1),  # upwind is for linear advection only
+    dict(scheme=2),
+    dict(scheme=1, p=1),  # FV stores one average per element: p = 0
+    dict(scheme=1, p=0, limiter=1),  # FV limits its slopes itself
 ]
 
 
