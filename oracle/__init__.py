@@ -28,7 +28,7 @@ _lib = None
 ADVECTION, EULER = 0, 1
 GAUSS, LOBATTO = 0, 1
 DIV_LP, DIV_CHAIN = 0, 1
-RUSANOV, UPWIND = 0, 1
+RUSANOV, UPWIND, ROE = 0, 1, 2
 PERIODIC, TRANSMISSIVE = 0, 1
 CPR, FV_MUSCL = 0, 1
 

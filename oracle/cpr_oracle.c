@@ -369,11 +369,76 @@ static void normal_speed_grad(const oracle_cfg* c, const double* q, double nx, d
  * lambda = max(|Vn(qm)| + c(qm), |Vn(qp)| + c(qp))  (reading: the paper does
  * not state lambda; the larger of the two one-sided speeds is taken).
  * Upwind (linear advection only): F = a_n qm if a_n >= 0, else a_n qp. */
+/* Roe's flux for the Euler equations along the unit normal (nx, ny):
+ *   F = (F_n(qm) + F_n(qp)) / 2 - (1/2) sum_k |lambda_k| alpha_k r_k
+ * over the characteristic fields of the Roe-averaged state (density
+ * sqrt(rho_m rho_p), velocity and total enthalpy averaged with weights
+ * sqrt(rho)): acoustic waves lambda = Vn -+ c with strengths
+ * (dp -+ rho c dVn) / (2 c^2), the entropy wave lambda = Vn with dRho -
+ * dp / c^2, the shear wave lambda = Vn with rho dVt (t = (-ny, nx)).
+ * Entropy fix of Harten and Hyman on the acoustic fields: with lambda_m,
+ * lambda_p the field's speed at the two states and delta = max(0, lambda -
+ * lambda_m, lambda_p - lambda) (positive only across a transonic
+ * rarefaction), |lambda| < delta is replaced by (lambda^2 + delta^2) /
+ * (2 delta); shocks and contacts keep the plain Roe flux. */
+/* |lambda| with the Harten-Hyman fix (lambda_m, lambda_p: the field's speed
+ * at the minus and plus states). */
+static double roe_fix(double lam, double lam_m, double lam_p)
+{
+    double d = 0.0;
+    if (lam - lam_m > d) d = lam - lam_m;
+    if (lam_p - lam > d) d = lam_p - lam;
+    double a = fabs(lam);
+    return a < d ? (lam * lam + d * d) / (2.0 * d) : a;
+}
+
+static void roe_flux(const oracle_cfg* c, const double* qm, const double* qp, double nx, double ny,
+                     double* F)
+{
+    double g = c->gamma;
+    double Fm[4], Fp[4];
+    normal_flux(c, qm, nx, ny, Fm);
+    normal_flux(c, qp, nx, ny, Fp);
+    double um = qm[1] / qm[0], vm = qm[2] / qm[0], up = qp[1] / qp[0], vp = qp[2] / qp[0];
+    double pm = pressure(g, qm), pp = pressure(g, qp);
+    double Hm = (qm[3] + pm) / qm[0], Hp = (qp[3] + pp) / qp[0];
+    double wm = sqrt(qm[0]), wp = sqrt(qp[0]);
+    double rho = wm * wp;
+    double u = (wm * um + wp * up) / (wm + wp);
+    double v = (wm * vm + wp * vp) / (wm + wp);
+    double H = (wm * Hm + wp * Hp) / (wm + wp);
+    double cs = sqrt((g - 1.0) * (H - 0.5 * (u * u + v * v)));
+    double vn = nx * u + ny * v, vt = -ny * u + nx * v;
+    double dr = qp[0] - qm[0], dp = pp - pm;
+    double dvn = (nx * up + ny * vp) - (nx * um + ny * vm);
+    double dvt = (-ny * up + nx * vp) - (-ny * um + nx * vm);
+    double a1 = (dp - rho * cs * dvn) / (2.0 * cs * cs);
+    double a2 = dr - dp / (cs * cs);
+    double a3 = rho * dvt;
+    double a4 = (dp + rho * cs * dvn) / (2.0 * cs * cs);
+    double cm = sqrt(g * pm / qm[0]), cp = sqrt(g * pp / qp[0]);
+    double vnm = nx * um + ny * vm, vnp = nx * up + ny * vp;
+    double l1 = roe_fix(vn - cs, vnm - cm, vnp - cp);
+    double l2 = fabs(vn);
+    double l4 = roe_fix(vn + cs, vnm + cm, vnp + cp);
+    double r1[4] = {1.0, u - cs * nx, v - cs * ny, H - vn * cs};
+    double r2[4] = {1.0, u, v, 0.5 * (u * u + v * v)};
+    double r3[4] = {0.0, -ny, nx, vt};
+    double r4[4] = {1.0, u + cs * nx, v + cs * ny, H + vn * cs};
+    for (int k = 0; k < 4; ++k)
+        F[k] = 0.5 * (Fm[k] + Fp[k]) -
+               0.5 * (l1 * a1 * r1[k] + l2 * a2 * r2[k] + l2 * a3 * r3[k] + l4 * a4 * r4[k]);
+}
+
 void oracle_common_flux(const oracle_cfg* c, const double* qm, const double* qp,
                         double nx, double ny, double* F)
 {
     int V = oracle_nvars(c);
-    if (c->eqn == OR_ADVECTION && c->flux == OR_UPWIND) {
+    if (c->eqn == OR_EULER && c->flux == OR_ROE) {
+        roe_flux(c, qm, qp, nx, ny, F);
+        return;
+    }
+    if (c->eqn == OR_ADVECTION && (c->flux == OR_UPWIND || c->flux == OR_ROE)) {
         double an = c->ax * nx + c->ay * ny;
         F[0] = an >= 0.0 ? an * qm[0] : an * qp[0];
         return;
@@ -833,7 +898,7 @@ static void element_residual_jvp(const oracle_cfg* c, const oracle_tab* T, const
 
 int oracle_residual_jvp(const oracle_cfg* c, const double* q, const double* dq, double* dR)
 {
-    if (check_cfg(c) || c->scheme != OR_CPR || c->div != OR_DIV_LP || !q || !dq || !dR) return -1;
+    if (check_cfg(c) || c->scheme != OR_CPR || c->div != OR_DIV_LP || c->flux == OR_ROE || !q || !dq || !dR) return -1;
     oracle_tab T;
     oracle_tables(c->p, c->pts, &T);
     long ne = (long)c->nx * c->ny;
@@ -961,7 +1026,7 @@ static void element_residual_vjp(const oracle_cfg* c, const oracle_tab* T, const
 
 int oracle_residual_vjp(const oracle_cfg* c, const double* q, const double* rbar, double* qbar)
 {
-    if (check_cfg(c) || c->scheme != OR_CPR || c->div != OR_DIV_LP || !q || !rbar || !qbar) return -1;
+    if (check_cfg(c) || c->scheme != OR_CPR || c->div != OR_DIV_LP || c->flux == OR_ROE || !q || !rbar || !qbar) return -1;
     oracle_tab T;
     oracle_tables(c->p, c->pts, &T);
     long N = oracle_state_size(c);
@@ -1193,7 +1258,7 @@ long oracle_run(const oracle_cfg* c, double* q, long nsteps, double dt, double t
 int oracle_rk3_vjp(const oracle_cfg* c, const double* q, double dt, const double* qbar_out,
                    double* qbar_in)
 {
-    if (check_cfg(c) || c->scheme != OR_CPR || c->div != OR_DIV_LP || !q || !qbar_out || !qbar_in) return -1;
+    if (check_cfg(c) || c->scheme != OR_CPR || c->div != OR_DIV_LP || c->flux == OR_ROE || !q || !qbar_out || !qbar_in) return -1;
     long N = oracle_state_size(c);
     double* R = (double*)malloc(sizeof(double) * N);
     double* q1 = (double*)malloc(sizeof(double) * N);

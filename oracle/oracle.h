@@ -35,7 +35,7 @@ extern "C" {
 enum { OR_ADVECTION = 0, OR_EULER = 1 };
 enum { OR_GAUSS = 0, OR_LOBATTO = 1 };
 enum { OR_DIV_LP = 0, OR_DIV_CHAIN = 1 };
-enum { OR_RUSANOV = 0, OR_UPWIND = 1 };
+enum { OR_RUSANOV = 0, OR_UPWIND = 1, OR_ROE = 2 };
 enum { OR_PERIODIC = 0, OR_TRANSMISSIVE = 1 };
 enum { OR_CPR = 0, OR_FV_MUSCL = 1 };
 
@@ -47,7 +47,8 @@ typedef struct {
     int pts;                 /* OR_GAUSS or OR_LOBATTO solution points        */
     int div;                 /* OR_DIV_LP (differentiate interpolated flux)   */
                              /* or OR_DIV_CHAIN (paper's chain rule, Sec 2.2) */
-    int flux;                /* OR_RUSANOV or OR_UPWIND (advection only)      */
+    int flux;                /* OR_RUSANOV, OR_UPWIND (advection only) or     */
+                             /* OR_ROE (Roe's linearised Riemann solver)      */
     double ax, ay;           /* advection velocity                            */
     double gamma;            /* ratio of specific heats (Euler)               */
     int bc_x, bc_y;          /* OR_PERIODIC or OR_TRANSMISSIVE                */
@@ -90,7 +91,13 @@ int oracle_point_coords(const oracle_cfg* c, double* x, double* y);
 
 /* Common (Riemann) flux through a face with unit normal (nx, ny) between the
  * state qm on the minus side and qp on the plus side (Sec. 4, Rusanov).
- * Pinned by consistency F(q,q) = f_n(q) and the swap symmetry. */
+ * Pinned by consistency F(q,q) = f_n(q) and the swap symmetry.
+ * OR_ROE: Roe's approximate Riemann solver (Roe-averaged states, the four
+ * characteristic fields of the 2D Euler equations along the normal) with
+ * the Harten-Hyman entropy fix on the two acoustic fields; for
+ * advection it is the upwind flux.  Pinned by consistency, swap symmetry, a
+ * stationary contact and a stationary normal shock resolved exactly, and
+ * pure upwinding of supersonic states. */
 void oracle_common_flux(const oracle_cfg* c, const double* qm, const double* qp,
                         double nx, double ny, double* F);
 
