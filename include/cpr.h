@@ -72,7 +72,9 @@ enum { CPR_SCHEME_CPR = 0, CPR_SCHEME_FV_MUSCL = 1 };            /* .scheme     
  *   pts      solution points: Gauss-Legendre or Gauss-Lobatto.
  *   corr     correction function: g_DG, the Radau polynomials (Sec. 2.2).
  *   flux     common flux: Rusanov (Sec. 4) for both equations, exact upwind
- *            for advection; CPR_FLUX_ROE returns CPR_ENOTIMPL.
+ *            for advection, or Roe's approximate Riemann solver with the
+ *            Harten-Hyman entropy fix (the upwind flux for advection); the
+ *            adjoint entry points and batches do not take CPR_FLUX_ROE.
  *   div      flux divergence: CPR_DIV_LP differentiates the Lagrange
  *            interpolant of the flux; CPR_DIV_CHAIN is the paper's chain rule
  *            A(q) dq/dxi (Sec. 2.2).

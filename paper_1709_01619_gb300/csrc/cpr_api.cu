@@ -147,7 +147,10 @@ bool cpr_fill_launch_cfg(const cpr_config* cfg, LaunchCfg* out)
     lc.eqn = cfg->eqn;
     lc.p = cfg->p;
     lc.div = cfg->div;
-    lc.flux = cfg->flux == CPR_FLUX_UPWIND ? cpr::FLUX_UPWIND : cpr::FLUX_RUSANOV;
+    // Roe's flux for advection is the upwind flux
+    lc.flux = cfg->flux == CPR_FLUX_UPWIND ? cpr::FLUX_UPWIND
+              : cfg->flux == CPR_FLUX_ROE   ? (cfg->eqn == CPR_EULER ? cpr::FLUX_ROE : cpr::FLUX_UPWIND)
+                                            : cpr::FLUX_RUSANOV;
     lc.nx = cfg->nx;
     lc.ny = cfg->ny;
     lc.bcx = cfg->bc_x == CPR_BC_TRANSMISSIVE;
@@ -232,10 +235,6 @@ extern "C" cpr_status cpr_init(const cpr_config* cfg, void* stream, cpr_ctx** ou
     if (const char* msg = cpr_validate_config(cfg)) {
         g_init_err = msg;
         return CPR_EINVAL;
-    }
-    if (cfg->flux == CPR_FLUX_ROE) {
-        g_init_err = "CPR_FLUX_ROE is not built";
-        return CPR_ENOTIMPL;
     }
     cpr_ctx* c = new (std::nothrow) cpr_ctx();
     if (!c) {
@@ -552,6 +551,7 @@ extern "C" cpr_status cpr_residual_vjp(cpr_ctx* c, const void* q, const void* rb
 {
     if (!c) return CPR_EINVAL;
     if (c->cfg.scheme == CPR_SCHEME_FV_MUSCL) return fail(c, CPR_EINVAL, "no adjoint for the FV scheme");
+    if (c->cfg.flux == CPR_FLUX_ROE) return fail(c, CPR_EINVAL, "no adjoint for the Roe flux");
     if (!q || !rbar || !qbar) return fail(c, CPR_EINVAL, "q_dev, rbar_dev and qbar_dev must be non-NULL");
     if (qbar == q || qbar == rbar) return fail(c, CPR_EINVAL, "qbar_dev must not alias q_dev or rbar_dev");
     if (!aligned(q) || !aligned(rbar) || !aligned(qbar)) return fail(c, CPR_EINVAL, "state arrays must be 16-byte aligned");
@@ -570,6 +570,7 @@ extern "C" cpr_status cpr_step_vjp(cpr_ctx* c, const void* q, const void* qbar_o
 {
     if (!c) return CPR_EINVAL;
     if (c->cfg.scheme == CPR_SCHEME_FV_MUSCL) return fail(c, CPR_EINVAL, "no adjoint for the FV scheme");
+    if (c->cfg.flux == CPR_FLUX_ROE) return fail(c, CPR_EINVAL, "no adjoint for the Roe flux");
     if (!q || !qbar_out || !qbar_in) return fail(c, CPR_EINVAL, "q_dev, qbar_out_dev and qbar_in_dev must be non-NULL");
     if (q == qbar_out || q == qbar_in) return fail(c, CPR_EINVAL, "q_dev must not alias the cotangents");
     if (!aligned(q) || !aligned(qbar_out) || !aligned(qbar_in))

@@ -14,7 +14,7 @@ constexpr int kAuxElems = 64; // elements per CTA in the element-wise passes
 
 enum { EQ_ADV = 0, EQ_EULER = 1 };
 enum { DIV_LP = 0, DIV_CHAIN = 1 };
-enum { FLUX_RUSANOV = 0, FLUX_UPWIND = 1 };
+enum { FLUX_RUSANOV = 0, FLUX_UPWIND = 1, FLUX_ROE = 2 };
 
 // What a stage-kernel launch computes (see cpr_stage.cuh).
 enum {
@@ -153,16 +153,85 @@ __device__ __forceinline__ void flux_jvp(const T* q, const T* dq, const Phys<T>&
     }
 }
 
+// |lambda| of an acoustic field with the Harten-Hyman entropy fix: lam_m,
+// lam_p are the field's speeds at the two states; only across a transonic
+// rarefaction (delta > 0) is |lambda| < delta smoothed.
+template <class T>
+__device__ __forceinline__ T roe_abs(T lam, T lam_m, T lam_p)
+{
+    T d = T(0);
+    d = lam - lam_m > d ? lam - lam_m : d;
+    d = lam_p - lam > d ? lam_p - lam : d;
+    const T a = lam >= T(0) ? lam : -lam;
+    return a < d ? (lam * lam + d * d) * frcp(T(2) * d) : a;
+}
+
+// Roe's flux for the Euler equations through an x-face (DIR 0) or y-face
+// (DIR 1): (f(qm) + f(qp))/2 - (1/2) sum_k |lambda_k| alpha_k r_k over the
+// acoustic, entropy and shear fields of the Roe-averaged state (density
+// sqrt(rho_m rho_p); velocity and total enthalpy averaged with weights
+// sqrt(rho)), with the Harten-Hyman fix on the acoustic fields.
+template <int DIR, class T>
+__device__ __forceinline__ void roe_flux(const T* qm, const T* qp, const Phys<T>& ph, T* F)
+{
+    const T g = ph.gamma;
+    T um, vm, rm, up, vp, rp;
+    const T pm = pressure(qm, g, um, vm, rm), pp = pressure(qp, g, up, vp, rp);
+    const T vnm = DIR == 0 ? um : vm, vnp = DIR == 0 ? up : vp;
+    T Fm[4], Fp[4];
+    Fm[0] = qm[0] * vnm;
+    Fp[0] = qp[0] * vnp;
+    Fm[1] = qm[1] * vnm + (DIR == 0 ? pm : T(0));
+    Fp[1] = qp[1] * vnp + (DIR == 0 ? pp : T(0));
+    Fm[2] = qm[2] * vnm + (DIR == 1 ? pm : T(0));
+    Fp[2] = qp[2] * vnp + (DIR == 1 ? pp : T(0));
+    Fm[3] = (qm[3] + pm) * vnm;
+    Fp[3] = (qp[3] + pp) * vnp;
+    const T Hm = (qm[3] + pm) * rm, Hp = (qp[3] + pp) * rp;
+    const T wm = fsqrt(qm[0]), wp = fsqrt(qp[0]), iw = frcp(wm + wp);
+    const T rho = wm * wp;
+    const T u = (wm * um + wp * up) * iw, v = (wm * vm + wp * vp) * iw, H = (wm * Hm + wp * Hp) * iw;
+    const T c2 = (g - T(1)) * (H - T(0.5) * (u * u + v * v));
+    const T cs = fsqrt(c2), ic2 = frcp(c2);
+    const T vn = DIR == 0 ? u : v;
+    const T vt = DIR == 0 ? v : -u;  // along t = (-n_y, n_x)
+    const T dvn = vnp - vnm;
+    const T dvt = DIR == 0 ? vp - vm : um - up;
+    const T dp = pp - pm;
+    const T a1 = (dp - rho * cs * dvn) * T(0.5) * ic2;
+    const T a2 = (qp[0] - qm[0]) - dp * ic2;
+    const T a3 = rho * dvt;
+    const T a4 = (dp + rho * cs * dvn) * T(0.5) * ic2;
+    const T cm = fsqrt(g * pm * rm), cp = fsqrt(g * pp * rp);
+    const T l1 = roe_abs(vn - cs, vnm - cm, vnp - cp);
+    const T l2 = vn >= T(0) ? vn : -vn;
+    const T l4 = roe_abs(vn + cs, vnm + cm, vnp + cp);
+    const T nx = DIR == 0 ? T(1) : T(0), ny = DIR == 0 ? T(0) : T(1);
+    const T r1[4] = {T(1), u - cs * nx, v - cs * ny, H - vn * cs};
+    const T r2[4] = {T(1), u, v, T(0.5) * (u * u + v * v)};
+    const T r3[4] = {T(0), -ny, nx, vt};
+    const T r4[4] = {T(1), u + cs * nx, v + cs * ny, H + vn * cs};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        F[k] = T(0.5) * (Fm[k] + Fp[k]) -
+               T(0.5) * (l1 * a1 * r1[k] + l2 * a2 * r2[k] + l2 * a3 * r3[k] + l4 * a4 * r4[k]);
+}
+
 // Common flux through an x-face (DIR 0, normal +x) or y-face (DIR 1, normal
 // +y) between qm (left/bottom) and qp (right/top).
 // Rusanov: F = (F(qm) + F(qp))/2 - lambda (qp - qm)/2 with lambda the larger
-// one-sided speed |Vn| + c.  Upwind (advection): F = a_n q_upwind.
+// one-sided speed |Vn| + c.  Upwind (advection; also Roe's flux there):
+// F = a_n q_upwind.  Roe (Euler): roe_flux.
 template <int EQ, int FLUX, int DIR, class T>
 __device__ __forceinline__ void common_flux(const T* qm, const T* qp, const Phys<T>& ph, T* F)
 {
+    if constexpr (EQ == EQ_EULER && FLUX == FLUX_ROE) {
+        roe_flux<DIR>(qm, qp, ph, F);
+        return;
+    }
     if constexpr (EQ == EQ_ADV) {
         T an = DIR == 0 ? ph.ax : ph.ay;
-        if constexpr (FLUX == FLUX_UPWIND) {
+        if constexpr (FLUX == FLUX_UPWIND || FLUX == FLUX_ROE) {
             F[0] = an >= T(0) ? an * qm[0] : an * qp[0];
         } else {
             T lam = an >= T(0) ? an : -an;
@@ -297,9 +366,25 @@ template <int EQ, int FLUX, int DIR, class T>
 __device__ __forceinline__ void common_flux_delta(const Ref<T>& r, const T* dm, const T* dp, const Phys<T>& ph,
                                                   T* G)
 {
+    if constexpr (EQ == EQ_EULER && FLUX == FLUX_ROE) {
+        // no difference form of Roe's flux: the flux of the full states,
+        // shifted to the reference
+        T qm[4], qp[4], F[4], f0[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            qm[k] = r.q[k] + dm[k];
+            qp[k] = r.q[k] + dp[k];
+        }
+        roe_flux<DIR>(qm, qp, ph, F);
+        if constexpr (DIR == 0) flux_x<EQ>(r.q, ph, f0);
+        else flux_y<EQ>(r.q, ph, f0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) G[k] = F[k] - f0[k];
+        return;
+    }
     if constexpr (EQ == EQ_ADV) {
         const T an = DIR == 0 ? ph.ax : ph.ay;
-        if constexpr (FLUX == FLUX_UPWIND) {
+        if constexpr (FLUX == FLUX_UPWIND || FLUX == FLUX_ROE) {
             G[0] = an >= T(0) ? an * dm[0] : an * dp[0];
         } else {
             const T lam = an >= T(0) ? an : -an;

@@ -13,7 +13,8 @@ cudaError_t launch_fv(const LaunchCfg& c, int mode, const StagePtrs& b, bool do_
     StageArgs<T> A = make_stage_args<T>(c, mode, b, do_wave);
     A.tiles_x = (c.nx + kFvTX - 1) / kFvTX;
     A.do_avg = 0;  // FV runs have no troubled-cell limiter, hence no averages pass
-    if (c.eqn == EQ_EULER) return fv_one<T, EQ_EULER, FLUX_RUSANOV>(c, A, s);
+    if (c.eqn == EQ_EULER)
+        return c.flux == FLUX_ROE ? fv_one<T, EQ_EULER, FLUX_ROE>(c, A, s) : fv_one<T, EQ_EULER, FLUX_RUSANOV>(c, A, s);
     if (c.flux == FLUX_UPWIND) return fv_one<T, EQ_ADV, FLUX_UPWIND>(c, A, s);
     return fv_one<T, EQ_ADV, FLUX_RUSANOV>(c, A, s);
 }

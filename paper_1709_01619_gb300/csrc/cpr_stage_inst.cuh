@@ -33,6 +33,9 @@ static cudaError_t stage_dispatch(const LaunchCfg& c, const StageArgs<T>& A, int
         return c.div == DIV_LP ? stage_one<T, P, EQ_ADV, DIV_LP, FLUX_RUSANOV>(c, A, ctas, s, prep)
                                : stage_one<T, P, EQ_ADV, DIV_CHAIN, FLUX_RUSANOV>(c, A, ctas, s, prep);
     }
+    if (c.flux == FLUX_ROE)
+        return c.div == DIV_LP ? stage_one<T, P, EQ_EULER, DIV_LP, FLUX_ROE>(c, A, ctas, s, prep)
+                               : stage_one<T, P, EQ_EULER, DIV_CHAIN, FLUX_ROE>(c, A, ctas, s, prep);
     return c.div == DIV_LP ? stage_one<T, P, EQ_EULER, DIV_LP, FLUX_RUSANOV>(c, A, ctas, s, prep)
                            : stage_one<T, P, EQ_EULER, DIV_CHAIN, FLUX_RUSANOV>(c, A, ctas, s, prep);
 }
