@@ -65,8 +65,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cpr", "reference"], default="cpr")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["vortex128", "vortex1024"], default="vortex128",
-                    help="vortex1024: only the HBM-sized case (a short run for profiling)")
+    ap.add_argument("--workload", choices=["vortex128", "vortex1024", "batch", "fv1536"], default="vortex128",
+                    help="vortex1024 / batch / fv1536: only that block (short runs for profiling)")
     ap.add_argument("--quick", action="store_true",
                     help="FP32 timed solves only (no FP64 solve, e2e, HBM case or CPU baseline)")
     return ap.parse_args()
@@ -408,6 +408,40 @@ def fv_case(peak, fp64_steps=200):
             "n_nonphys_final": nrm["n_nonphys"]}
 
 
+def paper_setting_case():
+    """The CPR variant the paper runs (Gauss-Lobatto solution points, the
+    chain-rule flux divergence, Sec. 2.2) on the same 128^2 p = 3 vortex to
+    t = 10 in FP32: throughput and the density-average error, next to the
+    headline setting (Gauss points, LP divergence)."""
+    import torch
+    from paper_1709_01619_gb300 import _native as nat
+    from paper_1709_01619_gb300 import inputs
+    cfg = nat.Config(eqn=nat.EULER, nx=NX, ny=NX, p=P, x1=L, y1=L, cfl=CFL, dtype=nat.F32,
+                     pts=nat.LOBATTO, div=nat.DIV_CHAIN)
+    with nat.Context(cfg) as ctx:
+        x, y = ctx.point_coords()
+        q0 = torch.tensor(inputs.vortex(x, y, eps=EPS), dtype=torch.float32, device="cuda")
+        q = q0.clone()
+        ctx.set_time(0.0, 0)
+        ctx.step(q, 20000, 0.0, T_END)
+        nsteps = ctx.get_time()[1]
+        q.copy_(q0)
+        ctx.set_time(0.0, 0)
+        torch.cuda.synchronize()
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev[0].record()
+        ctx.step(q, nsteps, 0.0, T_END)
+        ev[1].record()
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1])
+        avg = ctx.averages(q)[0].double().cpu().numpy()
+    # exact averages of the Lobatto run come from the same 10 x 10 rule
+    err = float(np.sqrt(np.mean((avg - exact_rho_averages(NX)) ** 2)))
+    dof = NX * NX * (P + 1) ** 2
+    return {"workload": "euler_vortex_128x128_p3_t10_lobatto_chainrule_fp32", "rk3_steps": nsteps, "ms": ms,
+            "dof_stage_per_s": dof * 3 * nsteps / (ms * 1e-3), "l2_rho_avg_error": err}
+
+
 def adjoint_case():
     """Gradient of J = 1/2 sum W (q_N - q_t)^2 with respect to the initial
     state: Euler vortex (strength 5) on [0,10]^2, 256^2, p = 3, FP32, 400
@@ -569,6 +603,7 @@ def run_cpr(args, world, rank, local):
     fv = fv_case(peak)
     fv["cpr_512_p2_over_fv_time_to_solution"] = limited["ms_fp32"] / fv["ms_fp32"]
     adj = adjoint_case()
+    paper = paper_setting_case()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, s, secs, thr = oracle_sample(12.0)
@@ -596,6 +631,7 @@ def run_cpr(args, world, rank, local):
         "limited": limited,
         "fv_equal_dof": fv,
         "adjoint": adj,
+        "paper_setting": paper,
         "f64": {"value": value64, "unit": UNIT, "ms_per_solve": ms64, "rk3_steps": n64,
                 "bound": "alu"},
         "l2_rho_avg_error": {"f32": err32, "f64": err64},
@@ -617,6 +653,10 @@ def main():
         run_reference(args, world, rank)
     elif args.workload == "vortex1024":
         run_hbm_only(args)
+    elif args.workload == "batch":
+        print(json.dumps(batch_case(peaks()[0], steps=max(1, args.steps), warmup=args.warmup)), flush=True)
+    elif args.workload == "fv1536":
+        print(json.dumps(fv_case(peaks()[0], fp64_steps=max(1, args.steps))), flush=True)
     else:
         run_cpr(args, world, rank, local)
     if world > 1:

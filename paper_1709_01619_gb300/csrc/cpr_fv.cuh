@@ -28,13 +28,14 @@ namespace cpr {
 
 constexpr int kFvTX = 32, kFvTY = 8;
 
-// Wrapped (periodic) or clamped (transmissive) element index.
+// Wrapped (periodic) or clamped (transmissive) element index, for indices
+// at most two outside [0, n) (no integer division: n may be 1).
 __device__ __forceinline__ int fv_ghost(int i, int n, int transmissive)
 {
-    if (i >= 0 && i < n) return i;
-    if (transmissive) return i < 0 ? 0 : n - 1;
-    i %= n;
-    return i < 0 ? i + n : i;
+    if (transmissive) return min(max(i, 0), n - 1);
+    while (i < 0) i += n;
+    while (i >= n) i -= n;
+    return i;
 }
 
 template <class T, int EQ, int FLUX>

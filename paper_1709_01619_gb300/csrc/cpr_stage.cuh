@@ -387,29 +387,30 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
     }
     {
         constexpr int NXH = 2 * TY * N, NYH = 2 * TX * N;
-        // one (line, variable) per thread and pass: all warps share the
-        // halo loads
-        for (int tv = tid; active && tv < V * (NXH + NYH); tv += NT) {
-            const int v = tv / (NXH + NYH), t = tv - v * (NXH + NYH);
+        // Halo line t for the variables v0, v0 + vstep, ... < V.  Every warp
+        // takes part: with NT a multiple of the line count each thread keeps
+        // one line (its index arithmetic done once) for NT / lines variables;
+        // otherwise one (line, variable) per thread and pass.
+        auto halo_line = [&](int t, int v0, int vstep) {
             const bool xdir = t < NXH;
             const int r0 = xdir ? t : t - NXH;
             const int side = xdir ? r0 / (TY * N) : r0 / (TX * N);
             const int r = xdir ? r0 % (TY * N) : r0 % (TX * N);
             const int pos = r / N, kk = r % N;  // pos: tile row (x) or tile column (y)
-            if (pos >= (xdir ? TYe : TXe)) continue;
+            if (pos >= (xdir ? TYe : TXe)) return;
             int gi, gj;
             if (xdir) {
                 gi = side ? i0 + TXe : i0 - 1;
                 gj = j0 + pos;
                 if (gi < 0 || gi >= A.nx) {
-                    if (A.bcx) continue;
+                    if (A.bcx) return;
                     gi = gi < 0 ? gi + A.nx : gi - A.nx;
                 }
             } else {
                 gi = i0 + pos;
                 gj = side ? j0 + TYe : j0 - 1;
                 if (gj < 0 || gj >= A.ny) {
-                    if (A.bcy) continue;
+                    if (A.bcy) return;
                     gj = gj < 0 ? gj + A.ny : gj - A.ny;
                 }
             }
@@ -417,7 +418,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
             const int lx = xdir ? (side ? TXe : -1) : pos;
             const int ly = xdir ? pos : (side ? TYe : -1);
             const T* coef = side ? tb.lm : tb.lp;  // the edge facing the tile
-            {
+            for (int v = v0; v < V; v += vstep) {
                 const T* src = A.qs + v * A.npts + eh * NN;
                 const T* srb = addb ? A.qb + v * A.npts + eh * NN : src;
                 T ref = T(0);
@@ -455,6 +456,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
                 }
                 if (DELTA && kk == 0) rfS[L::rf(v, lx, ly)] = ref;
             }
+        };
+        constexpr int LINES = NXH + NYH;
+        if constexpr (NT % LINES == 0) {
+            if (active) halo_line(tid % LINES, tid / LINES, NT / LINES);
+        } else {
+            for (int tv = tid; active && tv < V * LINES; tv += NT) halo_line(tv % LINES, tv / LINES, V);
         }
     }
     __syncthreads();
