@@ -76,9 +76,11 @@ struct StageLayout {
     // N = 4: rows of 16 bytes, element stride 16 words, row b of element el
     // stored at slot b ^ ((el >> 1) & 3).  A quarter warp's row accesses
     // (two elements) and a warp's column reads (eight elements, one word
-    // each) then both hit distinct banks.  Other N: padded element stride.
+    // each) then both hit distinct banks.  N = 3, 5: unpadded elements (the
+    // row reads of a warp are conflict-free, column reads at most two-way);
+    // N = 2: stride 6 (rows of 8 bytes stay aligned).
     static constexpr bool SWZ = N == 4;
-    static constexpr int ES = SWZ ? 16 : ((NN % 4 == 0) ? NN + 4 : ((NN + 3) / 4) * 4);
+    static constexpr int ES = SWZ ? 16 : (N == 2 ? 6 : NN);
     static constexpr int E = TX * TY;
     static constexpr int PE = (TX + 2) * (TY + 2);     // tile with its halo ring
     // The y-derivatives go over the dead tile copy in phase 3 (a buffer of
