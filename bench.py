@@ -65,8 +65,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cpr", "reference"], default="cpr")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["vortex128", "vortex1024", "batch", "fv1536"], default="vortex128",
-                    help="vortex1024 / batch / fv1536: only that block (short runs for profiling)")
+    ap.add_argument("--workload", choices=["vortex128", "vortex1024", "batch", "fv1536", "limited"],
+                    default="vortex128", help="vortex1024 / batch / fv1536 / limited: only that block "
+                    "(short runs for profiling)")
     ap.add_argument("--quick", action="store_true",
                     help="FP32 timed solves only (no FP64 solve, e2e, HBM case or CPU baseline)")
     return ap.parse_args()
@@ -655,6 +656,8 @@ def main():
         run_hbm_only(args)
     elif args.workload == "batch":
         print(json.dumps(batch_case(peaks()[0], steps=max(1, args.steps), warmup=args.warmup)), flush=True)
+    elif args.workload == "limited":
+        print(json.dumps(limited_case(peaks()[0], fp64_steps=max(1, args.steps))), flush=True)
     elif args.workload == "fv1536":
         print(json.dumps(fv_case(peaks()[0], fp64_steps=max(1, args.steps))), flush=True)
     else:

@@ -94,137 +94,191 @@ __global__ void __launch_bounds__(AuxShape<T, P, EQ>::EB) cpr_averages_kernel(co
     }
 }
 
-// TVB-modified minmod: keep the first argument when |a| <= M h^2.
-template <class T>
-__device__ __forceinline__ T minmod_tvb(T a, T b, T c, T M, T h)
+// Staging of EB consecutive elements by all NT threads of the CTA:
+// sm[(v * EB + le) * ES + pt] with the element stride ES = NN rounded up to
+// an odd number (a thread walking its own element meets no bank conflict).
+// For odd NN the block is a plain copy; a full block issues all of a
+// thread's loads before its first shared-memory store.
+template <int N>
+struct LimStride {
+    static constexpr int NN = N * N, ES = NN | 1;
+};
+
+template <int N, int V, int EB, int NT, class T>
+__device__ __forceinline__ void load_elements_all(const T* __restrict__ q, long long npts, long long e0, int cnt,
+                                                  T* sm)
 {
-    const T aa = a >= T(0) ? a : -a;
-    if (aa <= M * h * h) return a;
-    return minmod3(a, b, c);
+    constexpr int NN = N * N, ES = LimStride<N>::ES, PER = EB * NN, K = (PER + NT - 1) / NT;
+    if (cnt == EB) {
+        T r[V][K];
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int w = (int)threadIdx.x + k * NT;
+                if (PER % NT == 0 || w < PER) r[v][k] = q[v * npts + e0 * NN + w];
+            }
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int w = (int)threadIdx.x + k * NT;
+                if (PER % NT == 0 || w < PER) sm[v * EB * ES + (ES == NN ? w : (w / NN) * ES + w % NN)] = r[v][k];
+            }
+    } else {
+        for (int v = 0; v < V; ++v) {
+            const T* src = q + v * npts + e0 * NN;
+            for (int w = threadIdx.x; w < cnt * NN; w += NT) sm[v * EB * ES + (w / NN) * ES + w % NN] = src[w];
+        }
+    }
 }
 
-// Troubled-cell limiter.  One thread per element.
+// One edge point of the marking test, without branches.  d: the outward
+// edge deviation; c: the minmod of the two neighbour-average differences
+// across the edge (zero unless they share a sign); mh2 = M h^2.  The point is
+// troubled when |d| > M h^2 and |d - minmod(d, D+, D-)| > eps, where the
+// three-argument minmod is min(d, c) for d, c > 0, max(d, c) for d, c < 0,
+// else 0: the same values, and so the same decision, as the TVB minmod
+// written out.
+template <class T>
+__device__ __forceinline__ bool tvb_troubled(T d, T c, T mh2, T eps)
+{
+    const T mm = d > T(0) ? (c > T(0) ? ::fmin(d, c) : T(0)) : (c < T(0) ? ::fmax(d, c) : T(0));
+    const T r = d - mm;
+    return (d >= T(0) ? d : -d) > mh2 && (r >= T(0) ? r : -r) > eps;
+}
+
+// Troubled-cell limiter.  One thread per (element, variable), variable-major
+// in the CTA (thread v * EB + le), so that the loads of the neighbour
+// averages are coalesced and each thread holds one variable's N^2 values.
 // Marking (Algorithm 10): for every variable and every edge point, the
 // outward edge deviation delta = s (q_edge - qbar) (s = +1 on right/top edges,
 // -1 on left/bottom) is compared with the TVB minmod of delta and the
 // differences of the neighbouring averages across that edge; the element is
-// marked when |delta - mt| > eps anywhere (the OR over edge points of
-// Algorithm 11).  Limiting (Eq. 35, per direction): q_ab = qbar
-// + (xi_a hx / 2) mm(Dx+ / hx, Dx- / hx) + (eta_b hy / 2) mm(Dy+ / hy, Dy- / hy).
-// A transmissive boundary contributes a ghost average equal to the element's
-// own average.
+// marked when |delta - mt| > eps anywhere (the OR over edge points and
+// variables of Algorithm 11, taken in shared memory).  Limiting (Eq. 35, per
+// direction): q_ab = qbar + (xi_a hx / 2) mm(Dx+ / hx, Dx- / hx)
+// + (eta_b hy / 2) mm(Dy+ / hy, Dy- / hy).  A transmissive boundary
+// contributes a ghost average equal to the element's own average.  The fused
+// max signal speed splits an element's points over its V threads.
 template <class T, int P, int EQ>
-__global__ void __launch_bounds__(AuxShape<T, P, EQ>::EB) cpr_limit_kernel(const AuxArgs<T> A)
+struct LimShape {
+    static constexpr int V = NVars<EQ>::value, EB = AuxShape<T, P, EQ>::EB, NT = V * EB;
+};
+
+template <class T, int P, int EQ>
+__global__ void __launch_bounds__(LimShape<T, P, EQ>::NT) cpr_limit_kernel(const AuxArgs<T> A)
 {
     constexpr int N = P + 1, NN = N * N, V = NVars<EQ>::value, EB = AuxShape<T, P, EQ>::EB;
-    __shared__ T sm[V * EB * (NN + 1)];
+    constexpr int NT = LimShape<T, P, EQ>::NT;
+    constexpr int ES = LimStride<N>::ES;
+    __shared__ T sm[V * EB * ES];
+    __shared__ int s_mark[EB];
+    __shared__ int s_cnt;
     if (A.check_done && A.ctrl->done) return;  // uniform exit
     const long long e0 = (long long)blockIdx.x * EB;
     const int cnt = (int)min((long long)EB, A.ne - e0);
-    load_elements<N, V, EB>(A.q, A.npts, e0, cnt, sm);
-    __syncthreads();
-    const int le = threadIdx.x;
+    const int v = (int)threadIdx.x / EB, le = (int)threadIdx.x - v * EB;
     const Tab<T>& tb = A.tab;
-    int marked = 0;
-    T m = T(0);
-    if (le < cnt) {
-        const long long e = e0 + le;
-        const int i = (int)(e % A.nx), j = (int)(e / A.nx);
-        long long eL = i > 0 ? e - 1 : (A.bcx ? -1 : e + A.nx - 1);
-        long long eR = i < A.nx - 1 ? e + 1 : (A.bcx ? -1 : e - (A.nx - 1));
-        long long eB = j > 0 ? e - A.nx : (A.bcy ? -1 : e + (long long)A.nx * (A.ny - 1));
-        long long eT = j < A.ny - 1 ? e + A.nx : (A.bcy ? -1 : e - (long long)A.nx * (A.ny - 1));
-        T vals[V * NN];
-#pragma unroll
-        for (int v = 0; v < V; ++v)
-#pragma unroll
-            for (int pt = 0; pt < NN; ++pt) vals[v * NN + pt] = sm[(v * EB + le) * (NN + 1) + pt];
-        T worst = -T(1e30);
-        T qk[V], aL[V], aR[V], aB[V], aT[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            qk[v] = A.avg_in[v * A.ne + e];
-            aL[v] = eL >= 0 ? A.avg_in[v * A.ne + eL] : qk[v];
-            aR[v] = eR >= 0 ? A.avg_in[v * A.ne + eR] : qk[v];
-            aB[v] = eB >= 0 ? A.avg_in[v * A.ne + eB] : qk[v];
-            aT[v] = eT >= 0 ? A.avg_in[v * A.ne + eT] : qk[v];
-            const T dxp = aR[v] - qk[v], dxm = qk[v] - aL[v];
-            const T dyp = aT[v] - qk[v], dym = qk[v] - aB[v];
-#pragma unroll
-            for (int kk = 0; kk < N; ++kk) {
-                T row[N], col[N];
-#pragma unroll
-                for (int l = 0; l < N; ++l) {
-                    row[l] = vals[v * NN + kk * N + l];
-                    col[l] = vals[v * NN + l * N + kk];
-                }
-                T sL = tb.lm[0] * row[0], sR = tb.lp[0] * row[0];
-                T sB = tb.lm[0] * col[0], sT = tb.lp[0] * col[0];
-#pragma unroll
-                for (int l = 1; l < N; ++l) {
-                    sL = fma(tb.lm[l], row[l], sL);
-                    sR = fma(tb.lp[l], row[l], sR);
-                    sB = fma(tb.lm[l], col[l], sB);
-                    sT = fma(tb.lp[l], col[l], sT);
-                }
-                T d, dev;
-                d = qk[v] - sL;
-                dev = d - minmod_tvb(d, dxp, dxm, A.tvb_M, A.hx);
-                dev = (dev >= T(0) ? dev : -dev) - A.lim_eps;
-                worst = dev > worst ? dev : worst;
-                d = sR - qk[v];
-                dev = d - minmod_tvb(d, dxp, dxm, A.tvb_M, A.hx);
-                dev = (dev >= T(0) ? dev : -dev) - A.lim_eps;
-                worst = dev > worst ? dev : worst;
-                d = qk[v] - sB;
-                dev = d - minmod_tvb(d, dyp, dym, A.tvb_M, A.hy);
-                dev = (dev >= T(0) ? dev : -dev) - A.lim_eps;
-                worst = dev > worst ? dev : worst;
-                d = sT - qk[v];
-                dev = d - minmod_tvb(d, dyp, dym, A.tvb_M, A.hy);
-                dev = (dev >= T(0) ? dev : -dev) - A.lim_eps;
-                worst = dev > worst ? dev : worst;
-            }
-        }
-        marked = worst > T(0);
-        A.marks[e] = marked;
-        if (marked) {
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const T sx = minmod2((aR[v] - qk[v]) / A.hx, (qk[v] - aL[v]) / A.hx);
-                const T sy = minmod2((aT[v] - qk[v]) / A.hy, (qk[v] - aB[v]) / A.hy);
-#pragma unroll
-                for (int b = 0; b < N; ++b)
-#pragma unroll
-                    for (int a = 0; a < N; ++a) {
-                        const T x = (T(0.5) * A.hx * tb.xi[a]) * sx;
-                        const T y = (T(0.5) * A.hy * tb.xi[b]) * sy;
-                        const T val = (qk[v] + x) + y;
-                        vals[v * NN + b * N + a] = val;
-                        A.q[v * A.npts + e * NN + b * N + a] = val;
-                    }
-            }
-        }
-        if (A.do_wave) {
-#pragma unroll
-            for (int pt = 0; pt < NN; ++pt) {
-                T qp[V];
-#pragma unroll
-                for (int v = 0; v < V; ++v) qp[v] = vals[v * NN + pt];
-                const T s = point_speed<EQ>(qp, A.ph);
-                m = s > m ? s : m;
-            }
-        }
+    // own and neighbour averages first: their loads overlap the staging of
+    // the element values below
+    const long long e = e0 + min(le, max(cnt - 1, 0));
+    // element (i, j): 32-bit division when the grid allows it (a 64-bit
+    // division by a runtime value costs over a hundred instructions)
+    int i, j;
+    if (A.ne <= 0x7fffffffll) {
+        const int ei = (int)e;
+        j = ei / A.nx;
+        i = ei - j * A.nx;
+    } else {
+        j = (int)(e / A.nx);
+        i = (int)(e - (long long)j * A.nx);
     }
-    // count of marked elements (integer: order-independent)
-    __shared__ int s_cnt;
+    const long long eL = i > 0 ? e - 1 : (A.bcx ? -1 : e + A.nx - 1);
+    const long long eR = i < A.nx - 1 ? e + 1 : (A.bcx ? -1 : e - (A.nx - 1));
+    const long long eB = j > 0 ? e - A.nx : (A.bcy ? -1 : e + (long long)A.nx * (A.ny - 1));
+    const long long eT = j < A.ny - 1 ? e + A.nx : (A.bcy ? -1 : e - (long long)A.nx * (A.ny - 1));
+    const T* av = A.avg_in + v * A.ne;
+    const T qk = av[e];
+    const T aL = eL >= 0 ? av[eL] : qk, aR = eR >= 0 ? av[eR] : qk;
+    const T aB = eB >= 0 ? av[eB] : qk, aT = eT >= 0 ? av[eT] : qk;
+    load_elements_all<N, V, EB, NT>(A.q, A.npts, e0, cnt, sm);
+    if (threadIdx.x < EB) s_mark[threadIdx.x] = 0;
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
-    if (marked) atomicAdd(&s_cnt, 1);
+    T* mine = &sm[(v * EB + le) * ES];
+    if (le < cnt) {
+        T vals[NN];
+#pragma unroll
+        for (int pt = 0; pt < NN; ++pt) vals[pt] = mine[pt];
+        // minmod of the neighbour differences per direction (zero unless
+        // both share a sign), and M h^2 per direction
+        const T cx = minmod2(aR - qk, qk - aL), cy = minmod2(aT - qk, qk - aB);
+        const T mh2x = A.tvb_M * A.hx * A.hx, mh2y = A.tvb_M * A.hy * A.hy;
+        bool troubled = false;
+#pragma unroll
+        for (int kk = 0; kk < N; ++kk) {
+            T row[N], col[N];
+#pragma unroll
+            for (int l = 0; l < N; ++l) {
+                row[l] = vals[kk * N + l];
+                col[l] = vals[l * N + kk];
+            }
+            T sL = tb.lm[0] * row[0], sR = tb.lp[0] * row[0];
+            T sB = tb.lm[0] * col[0], sT = tb.lp[0] * col[0];
+#pragma unroll
+            for (int l = 1; l < N; ++l) {
+                sL = fma(tb.lm[l], row[l], sL);
+                sR = fma(tb.lp[l], row[l], sR);
+                sB = fma(tb.lm[l], col[l], sB);
+                sT = fma(tb.lp[l], col[l], sT);
+            }
+            troubled |= tvb_troubled(qk - sL, cx, mh2x, A.lim_eps);
+            troubled |= tvb_troubled(sR - qk, cx, mh2x, A.lim_eps);
+            troubled |= tvb_troubled(qk - sB, cy, mh2y, A.lim_eps);
+            troubled |= tvb_troubled(sT - qk, cy, mh2y, A.lim_eps);
+        }
+        if (troubled) s_mark[le] = 1;  // every writer stores 1
+    }
+    __syncthreads();
+    const int marked = le < cnt ? s_mark[le] : 0;
+    if (marked) {
+        const T sx = minmod2((aR - qk) / A.hx, (qk - aL) / A.hx);
+        const T sy = minmod2((aT - qk) / A.hy, (qk - aB) / A.hy);
+        T* dst = A.q + v * A.npts + e * NN;
+#pragma unroll
+        for (int b = 0; b < N; ++b)
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+                const T x = (T(0.5) * A.hx * tb.xi[a]) * sx;
+                const T y = (T(0.5) * A.hy * tb.xi[b]) * sy;
+                const T val = (qk + x) + y;
+                mine[b * N + a] = val;
+                dst[b * N + a] = val;
+            }
+    }
+    if (v == 0 && le < cnt) {
+        A.marks[e] = marked;
+        if (marked) atomicAdd(&s_cnt, 1);  // integer count: order-independent
+    }
     __syncthreads();
     if (threadIdx.x == 0 && s_cnt) atomicAdd(reinterpret_cast<unsigned long long*>(&A.ctrl->marked),
                                              (unsigned long long)s_cnt);
     if (A.do_wave) {
+        T m = T(0);
+        if (le < cnt) {
+#pragma unroll
+            for (int k = 0; k < (NN + V - 1) / V; ++k) {
+                const int pt = v + k * V;
+                if (pt < NN) {
+                    T qp[V];
+#pragma unroll
+                    for (int w = 0; w < V; ++w) qp[w] = sm[(w * EB + le) * ES + pt];
+                    const T s = point_speed<EQ>(qp, A.ph);
+                    m = s > m ? s : m;
+                }
+            }
+        }
         m = block_max<T>(m);
         last_cta_time_update<T>(m, A.wave, A.ctrl, /*advance=*/true, blockIdx.x, gridDim.x);
     }

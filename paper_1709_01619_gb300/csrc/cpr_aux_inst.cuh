@@ -116,7 +116,7 @@ static void elem_launch(bool lim, const AuxArgs<T>& A, cudaStream_t s)
 {
     constexpr int EB = AuxShape<T, P, EQ>::EB;
     const int grid = (int)((A.ne + EB - 1) / EB);
-    if (lim) cpr_limit_kernel<T, P, EQ><<<grid, EB, 0, s>>>(A);
+    if (lim) cpr_limit_kernel<T, P, EQ><<<grid, LimShape<T, P, EQ>::NT, 0, s>>>(A);
     else cpr_averages_kernel<T, P, EQ><<<grid, EB, 0, s>>>(A);
 }
 

@@ -499,20 +499,12 @@ __device__ __forceinline__ void common_flux_vjp(const T* qm, const T* qp, const 
     }
 }
 
-// Minmod functions of the limiter (Sec. 2.6).
+// Two-argument minmod of the limiter and of the MUSCL slopes (Sec. 2.6).
 template <class T>
 __device__ __forceinline__ T minmod2(T a, T b)
 {
     if (a > T(0) && b > T(0)) return a < b ? a : b;
     if (a < T(0) && b < T(0)) return a > b ? a : b;
-    return T(0);
-}
-
-template <class T>
-__device__ __forceinline__ T minmod3(T a, T b, T c)
-{
-    if (a > T(0) && b > T(0) && c > T(0)) return ::fmin(a, ::fmin(b, c));
-    if (a < T(0) && b < T(0) && c < T(0)) return ::fmax(a, ::fmax(b, c));
     return T(0);
 }
 

@@ -145,9 +145,17 @@ def test_config5_gradient_full_size_vs_fp64_differences():
     of dt = 7e-4 (t = 0.28, CFL 0.07 at the vortex's largest signal speed of
     about 3.9; 400 stable steps cannot reach t = 2),
     checkpoints every 20 steps; q_t is the forward solution from the vortex
-    of strength 4.5.  The FP32 adjoint gradient, projected on 32 random
-    directions, against central differences of J computed by the FP64 GPU
-    solver."""
+    of strength 4.5.
+
+    (1) The FP64 adjoint gradient projected on 16 random Gaussian directions d
+    against central differences of J (h = 1e-4) from the FP64 solver.  With
+    4.2 million entries a projection cancels by three to five orders of
+    magnitude, so the error is measured on the scale of the projection,
+    |g.d - fd| / (|g| |d|): the O(h^2) truncation of the difference keeps it
+    near 1e-9 (at most 3.4e-9 seen); bound 1e-8.
+    (2) The FP32 adjoint gradient against the FP64 one, relative L2 over the
+    whole vector: FP32 rounding accumulated over 1200 stages and their
+    adjoints (5.4e-5 seen); bound 2e-4."""
     n, nsteps, dt = 256, 400, 7e-4
     c32 = nat.Config(dtype=nat.F32, eqn=nat.EULER, nx=n, ny=n, p=3, x1=10.0, y1=10.0)
     c64 = nat.Config(dtype=nat.F64, eqn=nat.EULER, nx=n, ny=n, p=3, x1=10.0, y1=10.0)
@@ -163,14 +171,22 @@ def test_config5_gradient_full_size_vs_fp64_differences():
             ctx64.step(q, nsteps, dt)
             return float(0.5 * (W64 * (q - qt) ** 2).sum())
 
+        q64 = q0.clone().requires_grad_(True)
+        qN = adjoint.rollout(q64, ctx64, nsteps, dt, every=20)
+        (0.5 * (W64 * (qN - qt) ** 2).sum()).backward()
+        g64 = q64.grad.clone()
+
         q32 = q0.float().requires_grad_(True)
         qN = adjoint.rollout(q32, ctx32, nsteps, dt, every=20)
         W32 = adjoint.quadrature_weights(ctx32)
         (0.5 * (W32 * (qN - qt.float()) ** 2).sum()).backward()
-        g = q32.grad.double()
+        g32 = q32.grad.double()
+        assert float((g32 - g64).norm() / g64.norm()) <= 2e-4
+
         rng = np.random.default_rng(5)
         h = 1e-4
-        for _ in range(32):
+        for _ in range(16):
             d = torch.tensor(rng.standard_normal(c64.shape), device="cuda")
             fd = (J64(q0 + h * d) - J64(q0 - h * d)) / (2 * h)
-            assert float((g * d).sum()) == pytest.approx(fd, rel=2e-3)
+            scale = float(g64.norm() * d.norm())
+            assert abs(float((g64 * d).sum()) - fd) <= 1e-8 * scale
