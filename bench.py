@@ -54,7 +54,7 @@ MOVED_ARRAYS_PER_STEP = 10
 # from ncu captures of the stage kernel as it stands (profiles/): the
 # 128^2 workload replayed cold (writes stay in L2) and the 1024^2 case.
 NCU_TRAFFIC_128 = 8.433e6
-NCU_TRAFFIC_1024 = 8.582e8
+NCU_TRAFFIC_1024 = 8.578e8
 FALLBACK_HBM_GBS = 6800.0
 
 

@@ -237,10 +237,21 @@ constexpr bool stage_delta()
 #ifndef CPR_STAGE_MINB_FP32
 #define CPR_STAGE_MINB_FP32 4
 #endif
+#ifndef CPR_STAGE_MINB_FP32_N3
+#define CPR_STAGE_MINB_FP32_N3 6
+#endif
+#ifndef CPR_STAGE_MINB_FP32_N2
+#define CPR_STAGE_MINB_FP32_N2 4
+#endif
+#ifndef CPR_STAGE_MINB_FP32_N5
+#define CPR_STAGE_MINB_FP32_N5 3
+#endif
 template <class T, int N>
 constexpr int stage_min_blocks()
 {
-    return sizeof(T) == 8 ? 1 : (N <= 4 ? CPR_STAGE_MINB_FP32 : 3);
+    return sizeof(T) == 8 ? 1
+                          : (N == 2 ? CPR_STAGE_MINB_FP32_N2
+                                    : (N == 3 ? CPR_STAGE_MINB_FP32_N3 : (N == 4 ? CPR_STAGE_MINB_FP32 : CPR_STAGE_MINB_FP32_N5)));
 }
 
 // One tile of the stage: the work of one CTA.  tile indexes the instance's
