@@ -30,7 +30,8 @@ GAUSS, LOBATTO = 0, 1
 DIV_LP, DIV_CHAIN = 0, 1
 RUSANOV, UPWIND, ROE = 0, 1, 2
 PERIODIC, TRANSMISSIVE = 0, 1
-CPR, FV_MUSCL = 0, 1
+CPR, FV_MUSCL, FV_MUSCL3 = 0, 1, 2
+CORR_GDG, CORR_NDG, CORR_NDG_LUMPED = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -61,7 +62,7 @@ class _Cfg(ctypes.Structure):
         ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
         ("limiter", ctypes.c_int), ("tvb_M", ctypes.c_double),
         ("lim_eps", ctypes.c_double), ("cfl", ctypes.c_double),
-        ("scheme", ctypes.c_int),
+        ("scheme", ctypes.c_int), ("corr", ctypes.c_int),
     ]
 
 
@@ -97,6 +98,8 @@ def _load():
             lib.oracle_legendre_d.argtypes = [I, D]
             lib.oracle_tables.restype = I
             lib.oracle_tables.argtypes = [I, I, ctypes.POINTER(_Tab)]
+            lib.oracle_tables_corr.restype = I
+            lib.oracle_tables_corr.argtypes = [I, I, I, ctypes.POINTER(_Tab)]
             lib.oracle_state_size.restype = L
             lib.oracle_state_size.argtypes = [cp]
             for name in ("oracle_point_coords", "oracle_residual", "oracle_averages",
@@ -158,7 +161,8 @@ class Config:
     tvb_M: float = 0.0
     lim_eps: float = 1e-3
     cfl: float = 0.1
-    scheme: int = CPR  # FV_MUSCL: one average per element, p = 0
+    scheme: int = CPR  # FV_MUSCL / FV_MUSCL3: one average per element, p = 0
+    corr: int = CORR_GDG  # CPR edge correction: Radau g_DG, or the NDG lift
 
     @property
     def nvars(self) -> int:
@@ -193,9 +197,9 @@ def _check(rc, what):
         raise ValueError(f"oracle: {what} rejected its arguments")
 
 
-def tables(p: int, pts: int = GAUSS) -> dict:
+def tables(p: int, pts: int = GAUSS, corr: int = CORR_GDG) -> dict:
     t = _Tab()
-    _check(_load().oracle_tables(p, pts, ctypes.byref(t)), "tables")
+    _check(_load().oracle_tables_corr(p, pts, corr, ctypes.byref(t)), "tables")
     n = t.n
     return {
         "xi": np.array(t.xi[:n]), "w": np.array(t.w[:n]),

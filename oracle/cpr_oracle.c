@@ -195,6 +195,78 @@ int oracle_tables(int p, int pts, oracle_tab* T)
     return 0;
 }
 
+/* Solve the n x n system A x = b by Gaussian elimination with partial
+ * pivoting (A and b are overwritten); returns -1 if A is singular. */
+static int solve_dense(int n, double A[ORACLE_NMAX][ORACLE_NMAX], double* b, double* x)
+{
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        for (int r = k + 1; r < n; ++r)
+            if (fabs(A[r][k]) > fabs(A[piv][k])) piv = r;
+        if (A[piv][k] == 0.0) return -1;
+        if (piv != k) {
+            for (int m = 0; m < n; ++m) {
+                double t = A[k][m]; A[k][m] = A[piv][m]; A[piv][m] = t;
+            }
+            double t = b[k]; b[k] = b[piv]; b[piv] = t;
+        }
+        for (int r = k + 1; r < n; ++r) {
+            double f = A[r][k] / A[k][k];
+            for (int m = k; m < n; ++m) A[r][m] -= f * A[k][m];
+            b[r] -= f * b[k];
+        }
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        double s = b[k];
+        for (int m = k + 1; m < n; ++m) s -= A[k][m] * x[m];
+        x[k] = s / A[k][k];
+    }
+    return 0;
+}
+
+int oracle_tables_corr(int p, int pts, int corr, oracle_tab* T)
+{
+    if (oracle_tables(p, pts, T)) return -1;
+    if (corr == OR_CORR_GDG) return 0;
+    if (corr != OR_CORR_NDG && corr != OR_CORR_NDG_LUMPED) return -1;
+    int n = T->n;
+    /* Nodal DG, Sec. 2.3: dq/dt + D f - L [f.n - F_com] = 0 with the lifting
+     * matrix L = M^-1 M^A.  For the face xi = +1 of a tensor-product element
+     * M^A = l(+1) (x) M_1d, and M_2d = M_1d (x) M_1d, so L reduces to
+     * M_1d^-1 l(+1) along every line.  With n = +1 on the right face and -1
+     * on the left one this is the CPR form with g_R' = M^-1 l(+1) and
+     * g_L' = -M^-1 l(-1). */
+    double M[ORACLE_NMAX][ORACLE_NMAX];
+    if (corr == OR_CORR_NDG) {
+        double gx[ORACLE_NMAX + 1], gw[ORACLE_NMAX + 1];
+        gauss_nodes(n + 1, gx, gw); /* exact for the degree-2p integrands */
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                double s = 0.0;
+                for (int q = 0; q < n + 1; ++q)
+                    s += gw[q] * lagrange(n, T->xi, i, gx[q]) * lagrange(n, T->xi, j, gx[q]);
+                M[i][j] = s;
+            }
+    } else {
+        /* the integrals by the solution points' own quadrature */
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) M[i][j] = i == j ? T->w[i] : 0.0;
+    }
+    for (int side = 0; side < 2; ++side) {
+        double A[ORACLE_NMAX][ORACLE_NMAX], b[ORACLE_NMAX], x[ORACLE_NMAX];
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < n; ++j) A[i][j] = M[i][j];
+            b[i] = side ? T->lp[i] : T->lm[i];
+        }
+        if (solve_dense(n, A, b, x)) return -1;
+        for (int a = 0; a < n; ++a) {
+            if (side) T->dgr[a] = x[a];
+            else T->dgl[a] = -x[a];
+        }
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Sizes and coordinates                                                    */
 /* ------------------------------------------------------------------------ */
@@ -210,8 +282,8 @@ static int check_cfg(const oracle_cfg* c)
 {
     if (!c) return -1;
     if (c->eqn != OR_ADVECTION && c->eqn != OR_EULER) return -1;
-    if (c->scheme != OR_CPR && c->scheme != OR_FV_MUSCL) return -1;
-    if (c->scheme == OR_FV_MUSCL) {
+    if (c->scheme != OR_CPR && c->scheme != OR_FV_MUSCL && c->scheme != OR_FV_MUSCL3) return -1;
+    if (c->scheme != OR_CPR) {
         /* one average per element; the MUSCL limiter is part of the
          * reconstruction */
         if (c->nx < 1 || c->ny < 1 || c->p != 0 || c->limiter) return -1;
@@ -221,6 +293,7 @@ static int check_cfg(const oracle_cfg* c)
     }
     if (c->nx < 1 || c->ny < 1 || c->p < 1 || c->p > ORACLE_PMAX) return -1;
     if (!(c->x1 > c->x0) || !(c->y1 > c->y0)) return -1;
+    if (c->corr != OR_CORR_GDG && c->corr != OR_CORR_NDG && c->corr != OR_CORR_NDG_LUMPED) return -1;
     if (c->div == OR_DIV_CHAIN && c->eqn != OR_EULER && c->eqn != OR_ADVECTION) return -1;
     if (c->flux == OR_UPWIND && c->eqn != OR_ADVECTION) return -1;
     return 0;
@@ -229,7 +302,7 @@ static int check_cfg(const oracle_cfg* c)
 int oracle_point_coords(const oracle_cfg* c, double* x, double* y)
 {
     if (check_cfg(c)) return -1;
-    if (c->scheme == OR_FV_MUSCL) {
+    if (c->scheme != OR_CPR) {
         /* FV: the element centre stands for the element */
         double hx = (c->x1 - c->x0) / c->nx, hy = (c->y1 - c->y0) / c->ny;
         for (int j = 0; j < c->ny; ++j)
@@ -240,7 +313,7 @@ int oracle_point_coords(const oracle_cfg* c, double* x, double* y)
         return 0;
     }
     oracle_tab T;
-    oracle_tables(c->p, c->pts, &T);
+    oracle_tables_corr(c->p, c->pts, c->corr, &T);
     int n = T.n;
     double hx = (c->x1 - c->x0) / c->nx, hy = (c->y1 - c->y0) / c->ny;
     for (int j = 0; j < c->ny; ++j)
@@ -761,16 +834,45 @@ static double fv_slope(const oracle_cfg* c, const double* q, int v, int i, int j
     return minmod2(fwd, bwd);
 }
 
+/* Third-order MUSCL (Sec. 2.6; the paper gives no formula): van Leer's
+ * kappa-scheme with kappa = 1/3, the reconstruction that is exact for the
+ * averages of a parabola,
+ *   q_{i+1/2}^- = q_i + (1 - kappa)/4 D- + (1 + kappa)/4 D+,
+ * with each one-sided difference limited by minmod against b times the
+ * other, b = (3 - kappa)/(1 - kappa) = 4 (the largest b for which the face
+ * value stays between the neighbouring averages):
+ *   q_{i+1/2}^- = q_i + (1/6) mm(D-, 4 D+) + (1/3) mm(D+, 4 D-),
+ *   q_{i-1/2}^+ = q_i - (1/6) mm(D+, 4 D-) - (1/3) mm(D-, 4 D+),
+ * D+ = q_{i+1} - q_i, D- = q_i - q_{i-1} along direction d. */
+static void fv3_sides(const oracle_cfg* c, const double* q, int v, int i, int j, int d, double* up,
+                      double* down)
+{
+    int di = d == 0, dj = d == 1;
+    double qc = fv_cell(c, q, v, i, j);
+    double dp = fv_cell(c, q, v, i + di, j + dj) - qc;
+    double dm = qc - fv_cell(c, q, v, i - di, j - dj);
+    *up = qc + (minmod2(dm, 4.0 * dp) / 6.0 + minmod2(dp, 4.0 * dm) / 3.0);
+    *down = qc - (minmod2(dp, 4.0 * dm) / 6.0 + minmod2(dm, 4.0 * dp) / 3.0);
+}
+
 /* States on both sides of the face between element (i, j) and its +d
- * neighbour: each element's average moved half its limited change towards
- * the face. */
+ * neighbour.  Second order: each element's average moved half its limited
+ * change towards the face; third order: fv3_sides. */
 static void fv_face_states(const oracle_cfg* c, const double* q, int i, int j, int d,
                            double* qm, double* qp)
 {
     int V = oracle_nvars(c), di = d == 0, dj = d == 1;
     for (int v = 0; v < V; ++v) {
-        qm[v] = fv_cell(c, q, v, i, j) + 0.5 * fv_slope(c, q, v, i, j, d);
-        qp[v] = fv_cell(c, q, v, i + di, j + dj) - 0.5 * fv_slope(c, q, v, i + di, j + dj, d);
+        if (c->scheme == OR_FV_MUSCL3) {
+            double up, down;
+            fv3_sides(c, q, v, i, j, d, &up, &down);
+            qm[v] = up;
+            fv3_sides(c, q, v, i + di, j + dj, d, &up, &down);
+            qp[v] = down;
+        } else {
+            qm[v] = fv_cell(c, q, v, i, j) + 0.5 * fv_slope(c, q, v, i, j, d);
+            qp[v] = fv_cell(c, q, v, i + di, j + dj) - 0.5 * fv_slope(c, q, v, i + di, j + dj, d);
+        }
     }
 }
 
@@ -794,14 +896,14 @@ static void fv_element_residual(const oracle_cfg* c, const double* q, int i, int
 int oracle_residual(const oracle_cfg* c, const double* q, double* R)
 {
     if (check_cfg(c) || !q || !R) return -1;
-    if (c->scheme == OR_FV_MUSCL) {
+    if (c->scheme != OR_CPR) {
         long ne = (long)c->nx * c->ny;
 #pragma omp parallel for schedule(static)
         for (long e = 0; e < ne; ++e) fv_element_residual(c, q, (int)(e % c->nx), (int)(e / c->nx), R);
         return 0;
     }
     oracle_tab T;
-    oracle_tables(c->p, c->pts, &T);
+    oracle_tables_corr(c->p, c->pts, c->corr, &T);
     long ne = (long)c->nx * c->ny;
 #pragma omp parallel for schedule(static)
     for (long e = 0; e < ne; ++e) element_residual(c, &T, q, (int)(e % c->nx), (int)(e / c->nx), R);
@@ -900,7 +1002,7 @@ int oracle_residual_jvp(const oracle_cfg* c, const double* q, const double* dq, 
 {
     if (check_cfg(c) || c->scheme != OR_CPR || c->div != OR_DIV_LP || c->flux == OR_ROE || !q || !dq || !dR) return -1;
     oracle_tab T;
-    oracle_tables(c->p, c->pts, &T);
+    oracle_tables_corr(c->p, c->pts, c->corr, &T);
     long ne = (long)c->nx * c->ny;
 #pragma omp parallel for schedule(static)
     for (long e = 0; e < ne; ++e)
@@ -1028,7 +1130,7 @@ int oracle_residual_vjp(const oracle_cfg* c, const double* q, const double* rbar
 {
     if (check_cfg(c) || c->scheme != OR_CPR || c->div != OR_DIV_LP || c->flux == OR_ROE || !q || !rbar || !qbar) return -1;
     oracle_tab T;
-    oracle_tables(c->p, c->pts, &T);
+    oracle_tables_corr(c->p, c->pts, c->corr, &T);
     long N = oracle_state_size(c);
     memset(qbar, 0, sizeof(double) * N);
     long ne = (long)c->nx * c->ny;
@@ -1044,13 +1146,13 @@ int oracle_residual_vjp(const oracle_cfg* c, const double* q, const double* rbar
 int oracle_averages(const oracle_cfg* c, const double* q, double* avg)
 {
     if (check_cfg(c) || !q || !avg) return -1;
-    if (c->scheme == OR_FV_MUSCL) {
+    if (c->scheme != OR_CPR) {
         /* FV stores the averages themselves */
         memcpy(avg, q, sizeof(double) * oracle_nvars(c) * c->nx * c->ny);
         return 0;
     }
     oracle_tab T;
-    oracle_tables(c->p, c->pts, &T);
+    oracle_tables_corr(c->p, c->pts, c->corr, &T);
     int n = T.n, V = oracle_nvars(c);
     long ne = (long)c->nx * c->ny;
     for (int v = 0; v < V; ++v)
@@ -1092,7 +1194,7 @@ long oracle_limit(const oracle_cfg* c, double* q, int* marks, double* margin)
 {
     if (check_cfg(c) || c->scheme != OR_CPR || !q) return -1;
     oracle_tab T;
-    oracle_tables(c->p, c->pts, &T);
+    oracle_tables_corr(c->p, c->pts, c->corr, &T);
     int n = T.n, V = oracle_nvars(c);
     long ne = (long)c->nx * c->ny;
     double hx = (c->x1 - c->x0) / c->nx, hy = (c->y1 - c->y0) / c->ny;

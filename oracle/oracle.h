@@ -37,7 +37,8 @@ enum { OR_GAUSS = 0, OR_LOBATTO = 1 };
 enum { OR_DIV_LP = 0, OR_DIV_CHAIN = 1 };
 enum { OR_RUSANOV = 0, OR_UPWIND = 1, OR_ROE = 2 };
 enum { OR_PERIODIC = 0, OR_TRANSMISSIVE = 1 };
-enum { OR_CPR = 0, OR_FV_MUSCL = 1 };
+enum { OR_CPR = 0, OR_FV_MUSCL = 1, OR_FV_MUSCL3 = 2 };
+enum { OR_CORR_GDG = 0, OR_CORR_NDG = 1, OR_CORR_NDG_LUMPED = 2 };
 
 typedef struct {
     int eqn;                 /* OR_ADVECTION or OR_EULER                     */
@@ -58,7 +59,14 @@ typedef struct {
     double cfl;              /* CFL number for oracle_dt                      */
     int scheme;              /* OR_CPR, or OR_FV_MUSCL: one average per       */
                              /* element (p = 0), second-order MUSCL with      */
-                             /* minmod slopes (Sec. 2.1, 2.6, Algorithm 1)    */
+                             /* minmod slopes (Sec. 2.1, 2.6, Algorithm 1),   */
+                             /* or OR_FV_MUSCL3: third-order MUSCL (Sec. 2.6) */
+    int corr;                /* CPR edge correction: OR_CORR_GDG (Radau       */
+                             /* g_DG, Sec. 2.2), OR_CORR_NDG (the lifting     */
+                             /* operator M^-1 M^A of nodal DG, Sec. 2.3, with */
+                             /* the exact mass matrix) or OR_CORR_NDG_LUMPED  */
+                             /* (the same with the mass matrices integrated   */
+                             /* by the solution-point quadrature)             */
 } oracle_cfg;
 
 /* 1D operator tables for n = p + 1 points. */
@@ -81,6 +89,23 @@ double oracle_legendre_d(int k, double x);
  * Pinned by: numpy leggauss nodes/weights, exactness of D on monomials,
  * g_L(-1)=1, g_L(1)=0, sum_a w_a g_L'(xi_a) = -1 (tests/test_oracle_tables.py). */
 int oracle_tables(int p, int pts, oracle_tab* T);
+
+/* The same tables with dgl, dgr replaced by the edge-correction
+ * coefficients of corr:
+ *   OR_CORR_GDG         the Radau derivatives of oracle_tables;
+ *   OR_CORR_NDG         nodal DG in strong form (Sec. 2.3): the lifting
+ *                       matrix L = M^-1 M^A; on a tensor-product element it
+ *                       acts along each line with dgr = M^-1 l(+1),
+ *                       dgl = -M^-1 l(-1), M_ij = int l_i l_j over [-1, 1]
+ *                       (exact: Gauss rule of n + 1 points);
+ *   OR_CORR_NDG_LUMPED  the same with M integrated by the solution points'
+ *                       own quadrature (M = diag(w)).
+ * Pinned by: NDG equals the Radau derivatives (the equivalence of FR with
+ * g_DG and DG), lumped equals exact on Gauss points (the n-point rule is
+ * exact for degree 2p), the lumped Lobatto lift is +-p(p+1)/2 at the end
+ * node and zero elsewhere (end weight 2/(p(p+1))), and each lift integrates
+ * to +-1 (tests/test_oracle_ndg.py). */
+int oracle_tables_corr(int p, int pts, int corr, oracle_tab* T);
 
 /* Number of doubles in one state vector: V * nx * ny * (p+1)^2. */
 long oracle_state_size(const oracle_cfg* c);
