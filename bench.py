@@ -65,9 +65,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cpr", "reference"], default="cpr")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["vortex128", "vortex1024", "batch", "fv1536", "limited"],
-                    default="vortex128", help="vortex1024 / batch / fv1536 / limited: only that block "
-                    "(short runs for profiling)")
+    ap.add_argument("--workload", choices=["vortex128", "vortex1024", "batch", "fv1536", "limited", "radial"],
+                    default="vortex128", help="vortex1024 / batch / fv1536 / limited / radial: only that "
+                    "block (short runs for profiling)")
     ap.add_argument("--quick", action="store_true",
                     help="FP32 timed solves only (no FP64 solve, e2e, HBM case or CPU baseline)")
     return ap.parse_args()
@@ -401,12 +401,80 @@ def fv_case(peak, fp64_steps=200):
     torch.cuda.synchronize()
     ms64 = ev[0].elapsed_time(ev[1])
     ctx64.close()
+    cfg3 = nat.Config(eqn=nat.EULER, nx=n, ny=n, p=0, x1=1.0, y1=1.0, bc_x=nat.TRANSMISSIVE,
+                      bc_y=nat.TRANSMISSIVE, cfl=0.4, dtype=nat.F32, scheme=nat.SCHEME_FV_MUSCL3)
+    x, y = cfg_coords(cfg3)
+    ms3, n3, nrm3 = timed_solve(cfg3, inputs.four_quadrant(x, y), t_end)
     return {"workload": "euler_four_quadrant_fv_muscl_1536x1536_t0.3", "dof": dof, "rk3_steps": nsteps,
+            "muscl3": {"ms_fp32": ms3, "rk3_steps": n3, "dof_stage_per_s_fp32": dof * 3 * n3 / (ms3 * 1e-3),
+                       "n_nonphys_final": nrm3["n_nonphys"]},
             "ms_fp32": ms, "dof_stage_per_s_fp32": rate, "bound": "hbm", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak,
             "note": "state 37.7 MB per array: largely L2-resident",
             "dof_stage_per_s_fp64": dof * 3 * fp64_steps / (ms64 * 1e-3), "fp64_steps_timed": fp64_steps,
             "n_nonphys_final": nrm["n_nonphys"]}
+
+
+def timed_solve(cfg, q0_np, t_end, limit_first=False):
+    """One FP32/FP64 solve to t_end timed whole with CUDA events on the
+    context's stream (the step count is found by an untimed solve first).
+    Returns (ms, rk3 steps, norms of the result)."""
+    import torch
+    from paper_1709_01619_gb300 import _native as nat
+    with nat.Context(cfg) as ctx:
+        q0 = torch.tensor(q0_np, dtype=cfg.torch_dtype, device="cuda")
+        if limit_first:
+            ctx.limit(q0)
+        q = q0.clone()
+        ctx.set_time(0.0, 0)
+        ctx.step(q, 1000000, 0.0, t_end)
+        nsteps = ctx.get_time()[1]
+        q.copy_(q0)
+        ctx.set_time(0.0, 0)
+        torch.cuda.synchronize()
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev[0].record()
+        ctx.step(q, nsteps, 0.0, t_end)
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]), nsteps, ctx.norms(q)
+
+
+def radial_case():
+    """The paper's radially expanding shock tube (Sec. 4.2) at the size of
+    its P2 timing comparison, 1,440,000 DOF: (rho, p) = (1, 1) inside r < 0.4,
+    (0.125, 0.1) outside on [-1, 1]^2, transmissive, FP32 to t = 0.25.  CPR
+    400^2 p = 2 with the TVB limiter (M = 50, eps = 1e-3) at CFL 0.1 against
+    FV 1200^2 with second- and third-order MUSCL at CFL 0.4: time per RK3
+    step and to t = 0.25."""
+    from paper_1709_01619_gb300 import _native as nat
+    from paper_1709_01619_gb300 import inputs
+    t_end = 0.25
+    out = {"workload": "euler_radial_shock_tube_1440k_dof_t0.25"}
+    common = dict(eqn=nat.EULER, x0=-1.0, x1=1.0, y0=-1.0, y1=1.0, bc_x=nat.TRANSMISSIVE,
+                  bc_y=nat.TRANSMISSIVE, dtype=nat.F32)
+    cfg = nat.Config(nx=400, ny=400, p=2, limiter=1, tvb_M=50.0, lim_eps=1e-3, cfl=0.1, **common)
+    x, y = cfg_coords(cfg)
+    ms, n, nrm = timed_solve(cfg, inputs.radial_shock(x, y), t_end, limit_first=True)
+    out["cpr_400_p2"] = {"ms": ms, "rk3_steps": n, "ms_per_step": ms / n,
+                         "dof_stage_per_s": 400 * 400 * 9 * 3 * n / (ms * 1e-3),
+                         "n_marked_final": nrm["n_marked"], "n_nonphys_final": nrm["n_nonphys"]}
+    for key, scheme in (("fv_muscl2_1200", nat.SCHEME_FV_MUSCL), ("fv_muscl3_1200", nat.SCHEME_FV_MUSCL3)):
+        cfg = nat.Config(nx=1200, ny=1200, p=0, cfl=0.4, scheme=scheme, **common)
+        x, y = cfg_coords(cfg)
+        ms, n, nrm = timed_solve(cfg, inputs.radial_shock(x, y), t_end)
+        out[key] = {"ms": ms, "rk3_steps": n, "ms_per_step": ms / n,
+                    "dof_stage_per_s": 1200 * 1200 * 3 * n / (ms * 1e-3), "n_nonphys_final": nrm["n_nonphys"]}
+    c, f = out["cpr_400_p2"], out["fv_muscl2_1200"]
+    out["cpr_over_fv2_per_step"] = c["ms_per_step"] / f["ms_per_step"]
+    out["cpr_over_fv2_time_to_solution"] = c["ms"] / f["ms"]
+    return out
+
+
+def cfg_coords(cfg):
+    from paper_1709_01619_gb300 import _native as nat
+    with nat.Context(cfg) as ctx:
+        return ctx.point_coords()
 
 
 def paper_setting_case():
@@ -603,6 +671,7 @@ def run_cpr(args, world, rank, local):
     limited = limited_case(peak)
     fv = fv_case(peak)
     fv["cpr_512_p2_over_fv_time_to_solution"] = limited["ms_fp32"] / fv["ms_fp32"]
+    radial = radial_case()
     adj = adjoint_case()
     paper = paper_setting_case()
     cpu = None
@@ -631,6 +700,7 @@ def run_cpr(args, world, rank, local):
         "batch": batch,
         "limited": limited,
         "fv_equal_dof": fv,
+        "radial_shock_tube": radial,
         "adjoint": adj,
         "paper_setting": paper,
         "f64": {"value": value64, "unit": UNIT, "ms_per_solve": ms64, "rk3_steps": n64,
@@ -658,6 +728,8 @@ def main():
         print(json.dumps(batch_case(peaks()[0], steps=max(1, args.steps), warmup=args.warmup)), flush=True)
     elif args.workload == "limited":
         print(json.dumps(limited_case(peaks()[0], fp64_steps=max(1, args.steps))), flush=True)
+    elif args.workload == "radial":
+        print(json.dumps(radial_case()), flush=True)
     elif args.workload == "fv1536":
         print(json.dumps(fv_case(peaks()[0], fp64_steps=max(1, args.steps))), flush=True)
     else:

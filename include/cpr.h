@@ -57,12 +57,12 @@ typedef enum {
 
 enum { CPR_ADVECTION = 0, CPR_EULER = 1 };                       /* cpr_config.eqn  */
 enum { CPR_PTS_GAUSS = 0, CPR_PTS_LOBATTO = 1 };                 /* .pts            */
-enum { CPR_CORR_GDG = 0 };                                       /* .corr (Radau)   */
+enum { CPR_CORR_GDG = 0, CPR_CORR_NDG = 1, CPR_CORR_NDG_LUMPED = 2 }; /* .corr      */
 enum { CPR_FLUX_RUSANOV = 0, CPR_FLUX_UPWIND = 1, CPR_FLUX_ROE = 2 }; /* .flux      */
 enum { CPR_DIV_LP = 0, CPR_DIV_CHAIN = 1 };                      /* .div            */
 enum { CPR_BC_PERIODIC = 0, CPR_BC_TRANSMISSIVE = 1 };           /* .bc_x, .bc_y    */
 enum { CPR_F64 = 0, CPR_F32 = 1 };                               /* .dtype          */
-enum { CPR_SCHEME_CPR = 0, CPR_SCHEME_FV_MUSCL = 1 };            /* .scheme         */
+enum { CPR_SCHEME_CPR = 0, CPR_SCHEME_FV_MUSCL = 1, CPR_SCHEME_FV_MUSCL3 = 2 }; /* .scheme */
 
 /* Problem and scheme description.
  *   eqn      CPR_ADVECTION (u_t + ax u_x + ay u_y = 0) or CPR_EULER (Sec. 2).
@@ -70,7 +70,16 @@ enum { CPR_SCHEME_CPR = 0, CPR_SCHEME_FV_MUSCL = 1 };            /* .scheme     
  *   x0..y1   rectangular domain, x1 > x0, y1 > y0; uniform elements.
  *   p        polynomial order, 1 <= p <= 4 (p+1 points per direction).
  *   pts      solution points: Gauss-Legendre or Gauss-Lobatto.
- *   corr     correction function: g_DG, the Radau polynomials (Sec. 2.2).
+ *   corr     edge correction: CPR_CORR_GDG, the derivatives of the Radau
+ *            correction polynomials g_DG (Sec. 2.2); CPR_CORR_NDG, the
+ *            lifting operator M^-1 M^A of the nodal DG strong form (Sec.
+ *            2.3) with the exact mass matrix, which acts along each line
+ *            of the tensor-product element (the same scheme as g_DG, the
+ *            equivalence of DG and FR, with tables formed by a mass-matrix
+ *            solve); CPR_CORR_NDG_LUMPED, the same with the mass matrices
+ *            integrated by the solution points' own quadrature (equal to
+ *            the exact one on Gauss points; on Gauss-Lobatto points the
+ *            lift acts on the end points only, 'DG spectral element').
  *   flux     common flux: Rusanov (Sec. 4) for both equations, exact upwind
  *            for advection, or Roe's approximate Riemann solver with the
  *            Harten-Hyman entropy fix (the upwind flux for advection); the
@@ -91,7 +100,12 @@ enum { CPR_SCHEME_CPR = 0, CPR_SCHEME_FV_MUSCL = 1 };            /* .scheme     
  *            comparison scheme of the paper (Sec. 2.1), one average per
  *            element, face states by second-order MUSCL reconstruction with
  *            minmod-limited slopes (Sec. 2.6, Algorithm 1), the same common
- *            flux, boundary conditions, time stepping and CFL rule.  FV needs
+ *            flux, boundary conditions, time stepping and CFL rule; or
+ *            CPR_SCHEME_FV_MUSCL3, the same with the third-order MUSCL
+ *            reconstruction of Sec. 2.6 (van Leer's kappa = 1/3 face values,
+ *            each one-sided difference limited by minmod against four times
+ *            the other, so that a face state never leaves the range of the
+ *            two averages beside it).  FV needs
  *            p = 0 and limiter = 0 (pts, corr and div are ignored); its state
  *            is q[v][e] (one value per element, the element centre stands
  *            for the element in cpr_point_coords); cpr_limit, the adjoint

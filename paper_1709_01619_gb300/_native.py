@@ -19,12 +19,12 @@ from . import build as _build
 CPR_OK, CPR_EINVAL, CPR_ENOMEM, CPR_ECUDA, CPR_ENONPHYS, CPR_ETIMEOUT, CPR_ENOTIMPL = range(7)
 ADVECTION, EULER = 0, 1
 GAUSS, LOBATTO = 0, 1
-CORR_GDG = 0
+CORR_GDG, CORR_NDG, CORR_NDG_LUMPED = 0, 1, 2
 RUSANOV, UPWIND, ROE = 0, 1, 2
 DIV_LP, DIV_CHAIN = 0, 1
 PERIODIC, TRANSMISSIVE = 0, 1
 F64, F32 = 0, 1
-SCHEME_CPR, SCHEME_FV_MUSCL = 0, 1
+SCHEME_CPR, SCHEME_FV_MUSCL, SCHEME_FV_MUSCL3 = 0, 1, 2
 
 _STATUS = {0: "CPR_OK", 1: "CPR_EINVAL", 2: "CPR_ENOMEM", 3: "CPR_ECUDA", 4: "CPR_ENONPHYS",
            5: "CPR_ETIMEOUT", 6: "CPR_ENOTIMPL"}
@@ -92,7 +92,7 @@ class Config:
     lim_eps: float = 1e-3
     dtype: int = F64
     cfl: float = 0.1
-    scheme: int = 0  # SCHEME_CPR, or SCHEME_FV_MUSCL (p = 0: one average per element)
+    scheme: int = 0  # SCHEME_CPR, or SCHEME_FV_MUSCL / SCHEME_FV_MUSCL3 (p = 0: one average per element)
 
     @property
     def nvars(self) -> int:

@@ -164,7 +164,8 @@ bool cpr_fill_launch_cfg(const cpr_config* cfg, LaunchCfg* out)
     lc.ay = cfg->ay;
     lc.tvb_M = cfg->tvb_M;
     lc.lim_eps = cfg->lim_eps;
-    if (cpr::build_tables(cfg->p, cfg->pts, &lc.tab) != 0) return false;
+    lc.fv_order = cfg->scheme == CPR_SCHEME_FV_MUSCL3 ? 3 : 2;
+    if (cpr::build_tables(cfg->p, cfg->pts, cfg->corr, &lc.tab) != 0) return false;
     *out = lc;
     return true;
 }
@@ -178,16 +179,17 @@ const char* cpr_validate_config(const cpr_config* c)
     if (!(c->x1 > c->x0) || !(c->y1 > c->y0)) return "domain needs x1 > x0 and y1 > y0";
     if (!std::isfinite(c->x0) || !std::isfinite(c->x1) || !std::isfinite(c->y0) || !std::isfinite(c->y1))
         return "domain bounds must be finite";
-    if (c->scheme != CPR_SCHEME_CPR && c->scheme != CPR_SCHEME_FV_MUSCL)
-        return "scheme must be CPR_SCHEME_CPR or CPR_SCHEME_FV_MUSCL";
-    if (c->scheme == CPR_SCHEME_FV_MUSCL) {
-        if (c->p != 0) return "CPR_SCHEME_FV_MUSCL needs p = 0 (one average per element)";
-        if (c->limiter != 0) return "CPR_SCHEME_FV_MUSCL limits its slopes itself: limiter must be 0";
+    if (c->scheme != CPR_SCHEME_CPR && c->scheme != CPR_SCHEME_FV_MUSCL && c->scheme != CPR_SCHEME_FV_MUSCL3)
+        return "scheme must be CPR_SCHEME_CPR, CPR_SCHEME_FV_MUSCL or CPR_SCHEME_FV_MUSCL3";
+    if (c->scheme != CPR_SCHEME_CPR) {
+        if (c->p != 0) return "the FV schemes need p = 0 (one average per element)";
+        if (c->limiter != 0) return "the FV schemes limit their slopes themselves: limiter must be 0";
     } else if (c->p < 1 || c->p > 4) {
         return "p must be in [1, 4]";
     }
     if (c->pts != CPR_PTS_GAUSS && c->pts != CPR_PTS_LOBATTO) return "pts must be CPR_PTS_GAUSS or CPR_PTS_LOBATTO";
-    if (c->corr != CPR_CORR_GDG) return "corr must be CPR_CORR_GDG";
+    if (c->corr != CPR_CORR_GDG && c->corr != CPR_CORR_NDG && c->corr != CPR_CORR_NDG_LUMPED)
+        return "corr must be CPR_CORR_GDG, CPR_CORR_NDG or CPR_CORR_NDG_LUMPED";
     if (c->flux != CPR_FLUX_RUSANOV && c->flux != CPR_FLUX_UPWIND && c->flux != CPR_FLUX_ROE)
         return "flux must be CPR_FLUX_RUSANOV, CPR_FLUX_UPWIND or CPR_FLUX_ROE";
     if (c->flux == CPR_FLUX_UPWIND && c->eqn != CPR_ADVECTION) return "CPR_FLUX_UPWIND needs CPR_ADVECTION";
@@ -456,8 +458,8 @@ extern "C" cpr_status cpr_step_host(cpr_ctx* c, const void* qin, void* qout, int
 extern "C" cpr_status cpr_limit(cpr_ctx* c, void* q)
 {
     if (!c) return CPR_EINVAL;
-    if (c->cfg.scheme == CPR_SCHEME_FV_MUSCL)
-        return fail(c, CPR_EINVAL, "the FV scheme limits its slopes itself: no troubled-cell limiter");
+    if (c->cfg.scheme != CPR_SCHEME_CPR)
+        return fail(c, CPR_EINVAL, "the FV schemes limit their slopes themselves: no troubled-cell limiter");
     if (!q) return fail(c, CPR_EINVAL, "q_dev must be non-NULL");
     if (!aligned(q)) return fail(c, CPR_EINVAL, "state arrays must be 16-byte aligned");
     CPR_CUDA(c, averages(c, q, c->avg, c->stream));
@@ -550,7 +552,7 @@ static cpr_status vjp_check(cpr_ctx* c)
 extern "C" cpr_status cpr_residual_vjp(cpr_ctx* c, const void* q, const void* rbar, void* qbar)
 {
     if (!c) return CPR_EINVAL;
-    if (c->cfg.scheme == CPR_SCHEME_FV_MUSCL) return fail(c, CPR_EINVAL, "no adjoint for the FV scheme");
+    if (c->cfg.scheme != CPR_SCHEME_CPR) return fail(c, CPR_EINVAL, "no adjoint for the FV schemes");
     if (c->cfg.flux == CPR_FLUX_ROE) return fail(c, CPR_EINVAL, "no adjoint for the Roe flux");
     if (!q || !rbar || !qbar) return fail(c, CPR_EINVAL, "q_dev, rbar_dev and qbar_dev must be non-NULL");
     if (qbar == q || qbar == rbar) return fail(c, CPR_EINVAL, "qbar_dev must not alias q_dev or rbar_dev");
@@ -569,7 +571,7 @@ extern "C" cpr_status cpr_residual_vjp(cpr_ctx* c, const void* q, const void* rb
 extern "C" cpr_status cpr_step_vjp(cpr_ctx* c, const void* q, const void* qbar_out, void* qbar_in, double dt)
 {
     if (!c) return CPR_EINVAL;
-    if (c->cfg.scheme == CPR_SCHEME_FV_MUSCL) return fail(c, CPR_EINVAL, "no adjoint for the FV scheme");
+    if (c->cfg.scheme != CPR_SCHEME_CPR) return fail(c, CPR_EINVAL, "no adjoint for the FV schemes");
     if (c->cfg.flux == CPR_FLUX_ROE) return fail(c, CPR_EINVAL, "no adjoint for the Roe flux");
     if (!q || !qbar_out || !qbar_in) return fail(c, CPR_EINVAL, "q_dev, qbar_out_dev and qbar_in_dev must be non-NULL");
     if (q == qbar_out || q == qbar_in) return fail(c, CPR_EINVAL, "q_dev must not alias the cotangents");

@@ -6,8 +6,13 @@
 // the face states reconstructed by second-order MUSCL with minmod-limited
 // slopes (Sec. 2.6), q_face = q_i +- (1/2) minmod(q_{i+1} - q_i, q_i - q_{i-1}),
 // and the face flux from the same common flux as the CPR kernel
-// (reconstruct, then Riemann flux: Algorithm 1).  Ghost elements: periodic
-// directions wrap, transmissive ones repeat the boundary element.
+// (reconstruct, then Riemann flux: Algorithm 1).  ORDER 3 takes the
+// third-order MUSCL face values of Sec. 2.6 (van Leer's kappa = 1/3, each
+// one-sided difference D-, D+ limited by minmod against four times the other):
+//   q_{i+1/2}^- = q_i + mm(D-, 4 D+)/6 + mm(D+, 4 D-)/3,
+//   q_{i-1/2}^+ = q_i - mm(D+, 4 D-)/6 - mm(D-, 4 D+)/3,
+// on the same five-element stencil.  Ghost elements: periodic directions
+// wrap, transmissive ones repeat the boundary element.
 //
 // CTA: a tile of 32 x 8 elements, one thread per element.  Phase 1 stages
 // the tile with a ring of two elements in shared memory; phase 2 evaluates
@@ -38,7 +43,30 @@ __device__ __forceinline__ int fv_ghost(int i, int n, int transmissive)
     return i;
 }
 
-template <class T, int EQ, int FLUX>
+// Face states of element b (neighbours a below, c above along the line):
+// its value on the upper face (up) and on the lower face (down).
+template <int ORDER, class T>
+__device__ __forceinline__ T fv_up(T a, T b, T c)
+{
+    if constexpr (ORDER == 2) {
+        return b + T(0.5) * minmod2(c - b, b - a);
+    } else {
+        const T dm = b - a, dp = c - b;
+        return b + (minmod2(dm, T(4) * dp) * T(1.0 / 6.0) + minmod2(dp, T(4) * dm) * T(1.0 / 3.0));
+    }
+}
+template <int ORDER, class T>
+__device__ __forceinline__ T fv_down(T a, T b, T c)
+{
+    if constexpr (ORDER == 2) {
+        return b - T(0.5) * minmod2(c - b, b - a);
+    } else {
+        const T dm = b - a, dp = c - b;
+        return b - (minmod2(dp, T(4) * dm) * T(1.0 / 6.0) + minmod2(dm, T(4) * dp) * T(1.0 / 3.0));
+    }
+}
+
+template <class T, int EQ, int FLUX, int ORDER>
 __global__ void __launch_bounds__(kFvTX * kFvTY) cpr_fv_stage_kernel(const StageArgs<T> A)
 {
     constexpr int TX = kFvTX, TY = kFvTY, NT = TX * TY, HX = TX + 4, HY = TY + 4;
@@ -75,8 +103,8 @@ __global__ void __launch_bounds__(kFvTX * kFvTY) cpr_fv_stage_kernel(const Stage
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const T* r = &s[v][fj + 2][fi];  // elements fi-2 .. fi+1
-            qm[v] = r[1] + T(0.5) * minmod2(r[2] - r[1], r[1] - r[0]);
-            qp[v] = r[2] - T(0.5) * minmod2(r[3] - r[2], r[2] - r[1]);
+            qm[v] = fv_up<ORDER>(r[0], r[1], r[2]);
+            qp[v] = fv_down<ORDER>(r[1], r[2], r[3]);
         }
         common_flux<EQ, FLUX, 0>(qm, qp, A.ph, F);
 #pragma unroll
@@ -90,8 +118,8 @@ __global__ void __launch_bounds__(kFvTX * kFvTY) cpr_fv_stage_kernel(const Stage
         for (int v = 0; v < V; ++v) {
             const T a = s[v][fj][fi + 2], b = s[v][fj + 1][fi + 2], c = s[v][fj + 2][fi + 2],
                     d = s[v][fj + 3][fi + 2];  // elements fj-2 .. fj+1
-            qm[v] = b + T(0.5) * minmod2(c - b, b - a);
-            qp[v] = c - T(0.5) * minmod2(d - c, c - b);
+            qm[v] = fv_up<ORDER>(a, b, c);
+            qp[v] = fv_down<ORDER>(b, c, d);
         }
         common_flux<EQ, FLUX, 1>(qm, qp, A.ph, F);
 #pragma unroll
@@ -150,7 +178,8 @@ template <class T, int EQ, int FLUX>
 static cudaError_t fv_one(const LaunchCfg& c, const StageArgs<T>& A, cudaStream_t s)
 {
     const int ctas = ((c.nx + kFvTX - 1) / kFvTX) * ((c.ny + kFvTY - 1) / kFvTY);
-    cpr_fv_stage_kernel<T, EQ, FLUX><<<ctas, kFvTX * kFvTY, 0, s>>>(A);
+    if (c.fv_order == 3) cpr_fv_stage_kernel<T, EQ, FLUX, 3><<<ctas, kFvTX * kFvTY, 0, s>>>(A);
+    else cpr_fv_stage_kernel<T, EQ, FLUX, 2><<<ctas, kFvTX * kFvTY, 0, s>>>(A);
     return cudaGetLastError();
 }
 

@@ -17,13 +17,15 @@ struct HostTab {
     double dgl[kMaxN], dgr[kMaxN];
 };
 
-// Fill *t for order p and point family pts (0 Gauss-Legendre, 1
-// Gauss-Lobatto).  Returns 0 on success.
-int build_tables(int p, int pts, HostTab* t);
+// Fill *t for order p, point family pts (0 Gauss-Legendre, 1
+// Gauss-Lobatto) and edge correction corr (0 Radau g_DG, 1 nodal-DG lift
+// with the exact mass matrix, 2 with the lumped one).  Returns 0 on success.
+int build_tables(int p, int pts, int corr, HostTab* t);
 
 // Everything a launch needs, independent of the state dtype.
 struct LaunchCfg {
-    int eqn, p, div, flux;  // flux: FLUX_RUSANOV or FLUX_UPWIND
+    int eqn, p, div, flux;  // flux: FLUX_RUSANOV, FLUX_UPWIND or FLUX_ROE
+    int fv_order;           // FV schemes (p = 0): MUSCL order, 2 or 3
     int nx, ny, bcx, bcy;
     long long ne, npts;
     double hx, hy, gamma, ax, ay, tvb_M, lim_eps;

@@ -81,7 +81,7 @@ extern "C" cpr_status cpr_step_noalloc(const cpr_config* cfg, void* q_dev, int n
     if (cfg->eqn != CPR_ADVECTION && cfg->eqn != CPR_EULER) return CPR_EINVAL;
     if (cfg->nx < 1 || cfg->ny < 1 || cfg->nx > (1 << 20) || cfg->ny > (1 << 20) || cfg->p < 1 || cfg->p > 4 || !(cfg->x1 > cfg->x0) ||
         !(cfg->y1 > cfg->y0) || (cfg->pts != CPR_PTS_GAUSS && cfg->pts != CPR_PTS_LOBATTO) ||
-        cfg->corr != CPR_CORR_GDG || (cfg->div != CPR_DIV_LP && cfg->div != CPR_DIV_CHAIN) ||
+        (cfg->corr != CPR_CORR_GDG && cfg->corr != CPR_CORR_NDG && cfg->corr != CPR_CORR_NDG_LUMPED) || (cfg->div != CPR_DIV_LP && cfg->div != CPR_DIV_CHAIN) ||
         (cfg->flux != CPR_FLUX_RUSANOV && !(cfg->flux == CPR_FLUX_UPWIND && cfg->eqn == CPR_ADVECTION)) ||
         (cfg->bc_x != CPR_BC_PERIODIC && cfg->bc_x != CPR_BC_TRANSMISSIVE) ||
         (cfg->bc_y != CPR_BC_PERIODIC && cfg->bc_y != CPR_BC_TRANSMISSIVE) ||
@@ -123,7 +123,7 @@ extern "C" cpr_status cpr_step_noalloc(const cpr_config* cfg, void* q_dev, int n
     lc.tvb_M = cfg->tvb_M;
     lc.lim_eps = cfg->lim_eps;
     lc.ctrl = ctrl;
-    if (cpr::build_tables(cfg->p, cfg->pts, &lc.tab) != 0) return CPR_EINVAL;
+    if (cpr::build_tables(cfg->p, cfg->pts, cfg->corr, &lc.tab) != 0) return CPR_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool f32 = cfg->dtype == CPR_F32;
     e = f32 ? cpr::prepare_stage<float>(lc) : cpr::prepare_stage<double>(lc);

@@ -8,7 +8,10 @@
 //             D_al = (lambda_l / lambda_a) / (xi_a - xi_l), D_aa = -sum_{l != a} D_al.
 //   lm, lp    Lagrange basis at -1 and +1 (barycentric formula).
 //   dgl, dgr  derivatives of the g_DG correction functions (Radau polynomials,
-//             Sec. 2.2): g_L = (-1)^(p+1)/2 (P_{p+1} - P_p), g_R = (P_{p+1} + P_p)/2.
+//             Sec. 2.2): g_L = (-1)^(p+1)/2 (P_{p+1} - P_p), g_R = (P_{p+1} + P_p)/2;
+//             or the nodal-DG lift of Sec. 2.3 along a line, dgr = M^-1 l(+1),
+//             dgl = -M^-1 l(-1), with the 1D mass matrix M_ij = int l_i l_j
+//             (exact, by an (n+1)-point Gauss rule) or lumped (diag(w)).
 #include <cmath>
 
 #include "cpr_launch.h"
@@ -97,9 +100,74 @@ void lobatto(int n, double* x, double* w)
     }
 }
 
+// Lagrange basis polynomial l through the nodes xi, at x (product form).
+double lagrange_at(int n, const double* xi, int l, double x)
+{
+    double r = 1.0;
+    for (int m = 0; m < n; ++m)
+        if (m != l) r *= (x - xi[m]) / (xi[l] - xi[m]);
+    return r;
+}
+
+// x = M^-1 b for a small symmetric positive definite M (Cholesky).
+bool spd_solve(int n, const double (*M)[kMaxN], const double* b, double* x)
+{
+    double L[kMaxN][kMaxN] = {};
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double s = M[i][j];
+            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+            if (i == j) {
+                if (!(s > 0.0)) return false;
+                L[i][i] = std::sqrt(s);
+            } else {
+                L[i][j] = s / L[j][j];
+            }
+        }
+    }
+    double y[kMaxN];
+    for (int i = 0; i < n; ++i) {
+        double s = b[i];
+        for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
+        y[i] = s / L[i][i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = y[i];
+        for (int k = i + 1; k < n; ++k) s -= L[k][i] * x[k];
+        x[i] = s / L[i][i];
+    }
+    return true;
+}
+
+// Nodal-DG lift (Sec. 2.3): the strong form's L = M^-1 M^A reduces on a
+// tensor-product element to M^-1 l(+-1) along each line; with the outward
+// normal -1 on the left face the CPR form has dgl = -M^-1 l(-1).
+bool ndg_lift(int n, bool lumped, HostTab* t)
+{
+    double M[kMaxN][kMaxN] = {};
+    if (lumped) {
+        for (int i = 0; i < n; ++i) M[i][i] = t->w[i];
+    } else {
+        double gx[kMaxN + 1], gw[kMaxN + 1];
+        gauss(n + 1, gx, gw);
+        for (int q = 0; q < n + 1; ++q) {
+            double lq[kMaxN];
+            for (int i = 0; i < n; ++i) lq[i] = lagrange_at(n, t->xi, i, gx[q]);
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) M[i][j] += gw[q] * lq[i] * lq[j];
+        }
+    }
+    double x[kMaxN];
+    if (!spd_solve(n, M, t->lp, x)) return false;
+    for (int a = 0; a < n; ++a) t->dgr[a] = x[a];
+    if (!spd_solve(n, M, t->lm, x)) return false;
+    for (int a = 0; a < n; ++a) t->dgl[a] = -x[a];
+    return true;
+}
+
 }  // namespace
 
-int build_tables(int p, int pts, HostTab* t)
+int build_tables(int p, int pts, int corr, HostTab* t)
 {
     if (p == 0 && t) {
         // the one-point element of the FV scheme: the average itself at the
@@ -156,7 +224,8 @@ int build_tables(int p, int pts, HostTab* t)
         t->dgl[a] = 0.5 * s * (d1 - d0);
         t->dgr[a] = 0.5 * (d1 + d0);
     }
-    return 0;
+    if (corr == 1 || corr == 2) return ndg_lift(n, corr == 2, t) ? 0 : -1;
+    return corr == 0 ? 0 : -1;
 }
 
 }  // namespace cpr

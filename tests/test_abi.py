@@ -63,11 +63,13 @@ def test_struct_layouts_match_the_header(tmp_path):
 
 BAD = [
     dict(eqn=7), dict(nx=0), dict(ny=-3), dict(x1=0.0), dict(p=0), dict(p=5), dict(pts=2),
-    dict(corr=1), dict(flux=9), dict(div=3), dict(bc_x=4), dict(gamma=1.0), dict(limiter=2),
+    dict(corr=3), dict(corr=-1), dict(flux=9), dict(div=3), dict(bc_x=4), dict(gamma=1.0), dict(limiter=2),
     dict(tvb_M=-1.0), dict(lim_eps=-1.0), dict(dtype=5), dict(cfl=-0.1),
     dict(eqn=1, flux=1),  # upwind is for linear advection only
-    dict(scheme=2),
+    dict(scheme=3),
     dict(scheme=1, p=1),  # FV stores one average per element: p = 0
+    dict(scheme=2, p=2),
+    dict(scheme=2, p=0, limiter=1),
     dict(scheme=1, p=0, limiter=1),  # FV limits its slopes itself
 ]
 
@@ -98,6 +100,18 @@ def test_roe_flux_passes_validation(lib):
     needs a device)."""
     from paper_1709_01619_gb300 import _native
     cfg = _native.Config(flux=_native.ROE)
+    h = ctypes.c_void_p()
+    st = lib.cpr_init(ctypes.byref(cfg._c()), None, ctypes.byref(h))
+    assert st in (_native.CPR_OK, _native.CPR_ECUDA)
+    if st == _native.CPR_OK:
+        lib.cpr_destroy(h)
+
+
+@pytest.mark.parametrize("kw", [dict(corr=1), dict(corr=2, pts=1), dict(scheme=2, p=0),
+                                dict(scheme=1, p=0, corr=2)])
+def test_ndg_and_third_order_fv_pass_validation(lib, kw):
+    from paper_1709_01619_gb300 import _native
+    cfg = _native.Config(**kw)
     h = ctypes.c_void_p()
     st = lib.cpr_init(ctypes.byref(cfg._c()), None, ctypes.byref(h))
     assert st in (_native.CPR_OK, _native.CPR_ECUDA)

@@ -1,5 +1,6 @@
-"""FV MUSCL-minmod scheme (Sec. 2.1, 2.6, Algorithm 1) on the GPU against
-the FP64 oracle, through the C ABI: residual, fixed and CFL steps, the
+"""FV MUSCL-minmod schemes (Sec. 2.1, 2.6, Algorithm 1; second- and
+third-order reconstruction) on the GPU against the FP64 oracle, through the
+C ABI: residual, fixed and CFL steps, the
 conservation of the averages, and the four-quadrant problem of the equal-DOF
 comparison at full size (1536 x 1536 elements).
 
@@ -19,13 +20,17 @@ pytestmark = pytest.mark.gpu
 TOL64, TOL32 = 1e-12, 1e-5
 
 
+ORDERS = [nat.SCHEME_FV_MUSCL, nat.SCHEME_FV_MUSCL3]
+TO_ORACLE = {nat.SCHEME_FV_MUSCL: oracle.FV_MUSCL, nat.SCHEME_FV_MUSCL3: oracle.FV_MUSCL3}
+
+
 def make(dtype=nat.F64, **kw):
     kw.setdefault("p", 0)
     kw.setdefault("scheme", nat.SCHEME_FV_MUSCL)
     c = nat.Config(dtype=dtype, **kw)
     o = oracle.Config(eqn=c.eqn, nx=c.nx, ny=c.ny, p=0, x0=c.x0, x1=c.x1, y0=c.y0, y1=c.y1,
                       flux=c.flux, ax=c.ax, ay=c.ay, gamma=c.gamma, bc_x=c.bc_x, bc_y=c.bc_y,
-                      cfl=c.cfl, scheme=oracle.FV_MUSCL)
+                      cfl=c.cfl, scheme=TO_ORACLE[c.scheme])
     return c, o
 
 
@@ -66,10 +71,11 @@ CASES = [
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"eq{c['eqn']}-{c['nx']}x{c['ny']}-{c['kind']}")
 @pytest.mark.parametrize("dtype", [nat.F64, nat.F32])
-def test_residual_parity(case, dtype):
+@pytest.mark.parametrize("scheme", ORDERS)
+def test_residual_parity(case, dtype, scheme):
+    case = dict(case)
     kind = case.pop("kind")
-    c, o = make(dtype, **case)
-    case["kind"] = kind
+    c, o = make(dtype, scheme=scheme, **case)
     q = state(o, kind, 4)
     if dtype == nat.F32:
         q = q.astype(np.float32).astype(np.float64)
@@ -81,8 +87,9 @@ def test_residual_parity(case, dtype):
 
 @pytest.mark.parametrize("dtype", [nat.F64, nat.F32])
 @pytest.mark.parametrize("nsteps", [1, 2, 7])
-def test_fixed_steps(dtype, nsteps):
-    c, o = make(dtype, eqn=nat.EULER, nx=40, ny=24, x1=10.0, y1=6.0)
+@pytest.mark.parametrize("scheme", ORDERS)
+def test_fixed_steps(dtype, nsteps, scheme):
+    c, o = make(dtype, scheme=scheme, eqn=nat.EULER, nx=40, ny=24, x1=10.0, y1=6.0)
     q0 = state(o, "vortex", 8)
     if dtype == nat.F32:
         q0 = q0.astype(np.float32).astype(np.float64)
@@ -95,9 +102,10 @@ def test_fixed_steps(dtype, nsteps):
     assert rel(q, q_or) <= (TOL64 if dtype == nat.F64 else 1e-6)
 
 
-def test_cfl_steps_land_on_t_end():
-    c, o = make(nat.F64, eqn=nat.EULER, nx=48, ny=40, bc_x=nat.TRANSMISSIVE, bc_y=nat.TRANSMISSIVE,
-                cfl=0.4)
+@pytest.mark.parametrize("scheme", ORDERS)
+def test_cfl_steps_land_on_t_end(scheme):
+    c, o = make(nat.F64, scheme=scheme, eqn=nat.EULER, nx=48, ny=40, bc_x=nat.TRANSMISSIVE,
+                bc_y=nat.TRANSMISSIVE, cfl=0.4)
     q0 = state(o, "4q", 2)
     t_end = 0.05
     q_or, n_or, t_or = oracle.run(o, q0, 100000, 0.0, t_end)
@@ -110,8 +118,9 @@ def test_cfl_steps_land_on_t_end():
     assert rel(q, q_or) <= TOL64
 
 
-def test_averages_are_conserved_on_periodic_grid():
-    c, o = make(nat.F64, eqn=nat.EULER, nx=64, ny=48, x1=10.0, y1=7.5, cfl=0.4)
+@pytest.mark.parametrize("scheme", ORDERS)
+def test_averages_are_conserved_on_periodic_grid(scheme):
+    c, o = make(nat.F64, scheme=scheme, eqn=nat.EULER, nx=64, ny=48, x1=10.0, y1=7.5, cfl=0.4)
     q0 = state(o, "vortex", 5)
     with nat.Context(c) as ctx:
         qd = dev(q0, c)
@@ -121,12 +130,13 @@ def test_averages_are_conserved_on_periodic_grid():
     assert np.allclose(s1, s0, rtol=1e-13, atol=1e-12)
 
 
-def test_four_quadrant_full_size_one_step():
+@pytest.mark.parametrize("scheme", ORDERS)
+def test_four_quadrant_full_size_one_step(scheme):
     """The FV run of the equal-DOF comparison: 1536 x 1536 elements (the
     2,359,296 DOF of the 512^2 p = 2 CPR run), transmissive, CFL 0.4: one
     SSP-RK3 step at the CFL step size in FP64, against the oracle."""
-    c, o = make(nat.F64, eqn=nat.EULER, nx=1536, ny=1536, bc_x=nat.TRANSMISSIVE, bc_y=nat.TRANSMISSIVE,
-                cfl=0.4)
+    c, o = make(nat.F64, scheme=scheme, eqn=nat.EULER, nx=1536, ny=1536, bc_x=nat.TRANSMISSIVE,
+                bc_y=nat.TRANSMISSIVE, cfl=0.4)
     x, y = oracle.point_coords(o)
     q0 = inputs.four_quadrant(x, y)
     q_or, n, _ = oracle.run(o, q0, 1)
