@@ -339,27 +339,21 @@ extern "C" cpr_status cpr_residual(cpr_ctx* c, const void* q, void* r)
 // Enqueue one SSP-RK3 step on stream s (Sec. 4):
 //   q1 = q + dt R(q); q2 = 3/4 q + 1/4 (q1 + dt R(q1)); q = 1/3 q + 2/3 (q2 + dt R(q2)),
 // each stage result limited when the limiter is on.
+// The stage kernel of a limited run (the one that writes the averages)
+// clears the marked-element count for the limiter pass that follows it, and
+// skips that once t_end is reached, so the count survives the idle steps of
+// a run asked for more steps than it needs.
 static cudaError_t enqueue_step(cpr_ctx* c, void* q, cudaStream_t s)
 {
     const bool lim = c->cfg.limiter != 0;
     void* avg = lim ? c->avg : nullptr;
-    long long* marked = &c->ctrl->marked;
     cudaError_t e;
     if ((e = stage(c, 1, q, nullptr, c->q1, avg, false, s)) != cudaSuccess) return e;
-    if (lim) {
-        if ((e = cudaMemsetAsync(marked, 0, sizeof(long long), s)) != cudaSuccess) return e;
-        if ((e = limit(c, c->q1, c->avg, 1, s)) != cudaSuccess) return e;
-    }
+    if (lim && (e = limit(c, c->q1, c->avg, 1, s)) != cudaSuccess) return e;
     if ((e = stage(c, 2, c->q1, q, c->q2, avg, false, s)) != cudaSuccess) return e;
-    if (lim) {
-        if ((e = cudaMemsetAsync(marked, 0, sizeof(long long), s)) != cudaSuccess) return e;
-        if ((e = limit(c, c->q2, c->avg, 1, s)) != cudaSuccess) return e;
-    }
+    if (lim && (e = limit(c, c->q2, c->avg, 1, s)) != cudaSuccess) return e;
     if ((e = stage(c, 3, c->q2, q, q, avg, !lim, s)) != cudaSuccess) return e;
-    if (lim) {
-        if ((e = cudaMemsetAsync(marked, 0, sizeof(long long), s)) != cudaSuccess) return e;
-        if ((e = limit(c, q, c->avg, 2, s)) != cudaSuccess) return e;
-    }
+    if (lim && (e = limit(c, q, c->avg, 2, s)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 

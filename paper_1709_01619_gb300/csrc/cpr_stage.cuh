@@ -283,6 +283,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
     T* avS = xR;         // row partial sums of the averages, reuses xR after phase 3
 
     if (A.mode > 0 && A.ctrl->done) return;  // t_end reached: uniform exit
+    // a limited run: clear the marked-element count of the limiter pass
+    // that follows this stage (stream order keeps it apart from the last one)
+    if (A.mode > 0 && A.do_avg && tile == 0 && tid == 0) A.ctrl->marked = 0;
 
     const bool active = tid < NT;
     const int i0 = (tile % A.tiles_x) * TX;

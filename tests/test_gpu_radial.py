@@ -1,9 +1,9 @@
 """The radially expanding shock tube of Sec. 4.2 on the GPU: parity with the
 FP64 oracle for the limited CPR scheme and both FV schemes on small grids,
-and the full-size FP32 run of the paper's P2 comparison (400 x 400
-elements, p = 2, 1,440,000 DOF) to t = 0.25 checked by the problem's
-symmetry (x <-> y with the momenta swapped), positivity and, on the
-periodic square, the conservation of the average sums."""
+and the full-size runs of the paper's P2 comparison (400 x 400 elements,
+p = 2, 1,440,000 DOF) to t = 0.25: FP64 checked by the problem's symmetry
+(x <-> y with the momenta swapped), positivity and, on the periodic square,
+the conservation of the average sums; FP32 against the FP64 run."""
 import numpy as np
 import pytest
 import torch
@@ -71,32 +71,57 @@ def test_fv_matches_oracle_to_t_end(scheme, oscheme):
     assert rel(q, q_or) <= TOL64
 
 
-@pytest.mark.parametrize("bc", [nat.TRANSMISSIVE, nat.PERIODIC])
-def test_full_size_fp32_run_keeps_symmetry_and_positivity(bc):
-    """400 x 400, p = 2, TVB limiter, CFL 0.1, FP32 to t = 0.25.  The FP32
-    kernels evaluate the x- and y-lines with the same operations, so the
-    diagonal symmetry is kept to rounding: the bound 1e-5 (relative to the
-    state's norm) leaves room for a few limiter decisions taken differently
-    at mirrored points."""
+def full_size_run(dtype, bc):
     n = 400
-    c, _ = make(nat.F32, nx=n, ny=n, p=2, bc_x=bc, bc_y=bc, limiter=1, tvb_M=50.0, lim_eps=1e-3, cfl=0.1)
+    c, _ = make(dtype, nx=n, ny=n, p=2, bc_x=bc, bc_y=bc, limiter=1, tvb_M=50.0, lim_eps=1e-3, cfl=0.1)
     with nat.Context(c) as ctx:
         x, y = ctx.point_coords()
-        qd = torch.tensor(inputs.radial_shock(x, y), dtype=torch.float32, device="cuda")
+        qd = torch.tensor(inputs.radial_shock(x, y), dtype=c.torch_dtype, device="cuda")
         ctx.limit(qd)
         s0 = np.array(ctx.norms(qd)["sum_avg"])
         ctx.step(qd, 100000, 0.0, 0.25)
         t, steps = ctx.get_time()
         nrm = ctx.norms(qd)
-        q = host(qd)
-    assert t == 0.25 and steps > 100
-    assert nrm["n_nonphys"] == 0
-    g = q.reshape(4, n, n, 3, 3)
-    gt = g.transpose(0, 2, 1, 4, 3)
-    scale = np.linalg.norm(g)
-    err = np.linalg.norm(np.stack([g[0] - gt[0], g[1] - gt[2], g[2] - gt[1], g[3] - gt[3]]))
-    assert err <= 1e-5 * scale
+        return host(qd).reshape(4, n, n, 3, 3), t, steps, s0, nrm
+
+
+@pytest.mark.parametrize("bc", [nat.TRANSMISSIVE, nat.PERIODIC])
+def test_full_size_run_symmetry_positivity_and_fp32_difference(bc):
+    """400 x 400, p = 2, TVB limiter, CFL 0.1, to t = 0.25 (1046 steps).
+    FP64: the x <-> y symmetry holds to rounding (1e-11 with transmissive
+    boundaries, 1e-15 periodic, seen; bound 1e-9), every state is physical,
+    the limiter marks elements, and on the periodic square the average sums
+    are constant.  FP32: physical, and within 5e-3 relative L2 of the FP64
+    run (1.9e-3 transmissive, 2.1e-4 periodic, seen: rounding differences
+    that the limiter's marking decisions carry along the shocks, far below
+    the scheme's own error on this discontinuous problem)."""
+    g64, t, steps, s0, nrm = full_size_run(nat.F64, bc)
+    assert t == 0.25 and steps > 1000
+    assert nrm["n_nonphys"] == 0 and nrm["n_marked"] > 0
+    gt = g64.transpose(0, 2, 1, 4, 3)
+    err = np.linalg.norm(np.stack([g64[0] - gt[0], g64[1] - gt[2], g64[2] - gt[1], g64[3] - gt[3]]))
+    assert err <= 1e-9 * np.linalg.norm(g64)
     if bc == nat.PERIODIC:
         s1 = np.array(nrm["sum_avg"])
-        assert np.allclose(s1[[0, 3]], s0[[0, 3]], rtol=1e-5)
-        assert np.abs(s1[1:3]).max() <= 1e-5 * np.abs(s0[0])
+        assert np.abs(s1 - s0).max() <= 1e-11 * np.abs(s0).max()
+    g32, t32, steps32, _, nrm32 = full_size_run(nat.F32, bc)
+    assert t32 == 0.25 and nrm32["n_nonphys"] == 0 and nrm32["n_marked"] > 0
+    assert rel(g32, g64) <= 5e-3
+
+
+def test_marked_count_survives_idle_steps():
+    """A run asked for more steps than t_end needs ends with idle steps; the
+    count of marked elements still reports the last limiter pass."""
+    c, _ = make(nx=64, ny=64, p=2, bc_x=nat.TRANSMISSIVE, bc_y=nat.TRANSMISSIVE, limiter=1, tvb_M=50.0,
+                lim_eps=1e-3, cfl=0.1)
+    with nat.Context(c) as ctx:
+        x, y = ctx.point_coords()
+        q0 = torch.tensor(inputs.radial_shock(x, y), dtype=torch.float64, device="cuda")
+        q = q0.clone()
+        ctx.step(q, 100000, 0.0, 0.05)
+        n = ctx.get_time()[1]
+        m_idle = ctx.norms(q)["n_marked"]
+        q = q0.clone()
+        ctx.set_time(0.0, 0)
+        ctx.step(q, n, 0.0, 0.05)
+        assert ctx.norms(q)["n_marked"] == m_idle > 0
