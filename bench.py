@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--workload", choices=["vortex128", "vortex1024", "batch", "fv1536", "limited", "radial"],
                     default="vortex128", help="vortex1024 / batch / fv1536 / limited / radial: only that "
                     "block (short runs for profiling)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="--workload batch: the untuned launch (for profilers, whose serialised replays "
+                    "distort the autotuner's timings)")
     ap.add_argument("--quick", action="store_true",
                     help="FP32 timed solves only (no FP64 solve, e2e, HBM case or CPU baseline)")
     return ap.parse_args()
@@ -265,10 +268,13 @@ def hbm_case(make, peak, steps=HBM_STEPS):
             "dof_stage_per_s": dofH * 3 * steps / (msH * 1e-3), "rk3_steps": steps}
 
 
-def batch_case(peak, steps=100, warmup=3):
+def batch_case(peak, steps=100, warmup=3, tune=True):
     """64 isentropic-vortex instances (N ~ U{32..256}, p ~ U{2,3,4}, strength
     ~ U[1,5], numpy seed 0) on [0,10]^2 in FP32, advanced together by the
-    batched solver with per-instance CFL steps after autotuning."""
+    batched solver with per-instance CFL steps after autotuning (tune=False:
+    the untuned launch, one CTA per tile of the 8x8 family, which is what the
+    autotuner picks on GB300; a profiler's serialised replays would distort
+    its timings)."""
     import torch
     from paper_1709_01619_gb300 import _native as nat
     from paper_1709_01619_gb300 import inputs
@@ -282,7 +288,7 @@ def batch_case(peak, steps=100, warmup=3):
         qs.append(torch.tensor(inputs.vortex(x, y, eps=s["eps"]), dtype=torch.float32, device="cuda"))
     dof = sum(c.nx * c.ny * (c.p + 1) ** 2 for c in cfgs)
     with nat.Batch(cfgs) as b:
-        choices = b.tune(qs)
+        choices = b.tune(qs) if tune else []
         b.step(qs, warmup)
         torch.cuda.synchronize()
         ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -296,7 +302,7 @@ def batch_case(peak, steps=100, warmup=3):
     return {"workload": "batch_64_vortex_N32-256_p2-4_fp32", "instances": len(cfgs), "dof": dof,
             "rk3_steps": steps, "ms": ms, "dof_stage_per_s": rate, "bound": "hbm",
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "tuned": [{"p": p, "family": f, "grid": g} for p, f, g in choices]}
+            "tuned": [{"p": p, "family": f, "grid": g} for p, f, g in choices] if tune else None}
 
 
 def limited_case(peak, fp64_steps=100):
@@ -725,7 +731,8 @@ def main():
     elif args.workload == "vortex1024":
         run_hbm_only(args)
     elif args.workload == "batch":
-        print(json.dumps(batch_case(peaks()[0], steps=max(1, args.steps), warmup=args.warmup)), flush=True)
+        print(json.dumps(batch_case(peaks()[0], steps=max(1, args.steps), warmup=args.warmup,
+                                    tune=not args.no_tune)), flush=True)
     elif args.workload == "limited":
         print(json.dumps(limited_case(peaks()[0], fp64_steps=max(1, args.steps))), flush=True)
     elif args.workload == "radial":

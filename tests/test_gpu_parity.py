@@ -322,6 +322,38 @@ def test_limiter_parity(dtype, pts):
     assert rel_l2(a, b) <= (TOL64 if dtype == nat.F64 else TOL32)
 
 
+@pytest.mark.parametrize("dtype", [nat.F64, nat.F32])
+@pytest.mark.parametrize("p", [1, 3, 4])
+@pytest.mark.parametrize("eqn", [nat.EULER, nat.ADVECTION])
+def test_limiter_parity_other_orders(eqn, p, dtype):
+    """The limiter kernel (one thread per element and variable) for the
+    other orders and for one variable: 41 x 23 elements (a ragged last
+    block), periodic in x, transmissive in y."""
+    kw = dict(flux=nat.UPWIND, ax=0.9, ay=-0.6) if eqn == nat.ADVECTION else {}
+    c, o = make(dtype=dtype, eqn=eqn, nx=41, ny=23, p=p, bc_x=nat.PERIODIC, bc_y=nat.TRANSMISSIVE,
+                limiter=1, tvb_M=20.0, lim_eps=1e-3, **kw)
+    if eqn == nat.EULER:
+        q = inputs.perturbed(_four_quadrant(o), 3 + p, 2e-3)
+    else:
+        x, y = oracle.point_coords(o)
+        q = (np.where(x + 0.5 * y > 0.6, 1.0, 0.2) + 0.05 * np.sin(7 * x))[None]
+    if dtype == nat.F32:
+        q = q.astype(np.float32).astype(np.float64)
+    q_or, marks_or, margin, cnt = oracle.limit(o, q)
+    with nat.Context(c) as ctx:
+        qd = to_dev(q, c)
+        ctx.limit(qd)
+        marks = ctx.get_marks()
+        ql = host(qd)
+        n_marked = ctx.norms(qd)["n_marked"]
+    sure = np.abs(margin) > (1e-10 if dtype == nat.F64 else 1e-4)
+    assert np.array_equal(marks[sure], marks_or[sure])
+    assert n_marked == marks.sum() and cnt > 10
+    agree = marks == marks_or
+    assert agree.mean() > 0.99
+    assert rel_l2(ql[:, agree, :], q_or[:, agree, :]) <= (TOL64 if dtype == nat.F64 else TOL32)
+
+
 def test_steps_with_limiter_fp64():
     c, o = make(eqn=nat.EULER, nx=40, ny=40, p=2, bc_x=nat.TRANSMISSIVE, bc_y=nat.TRANSMISSIVE,
                 limiter=1, tvb_M=50.0, lim_eps=1e-3, cfl=0.1)
