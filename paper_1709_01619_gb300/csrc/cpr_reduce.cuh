@@ -86,9 +86,21 @@ __device__ __forceinline__ void last_cta_time_update(T m, T* partial, Ctrl* ctrl
     __syncthreads();
     if (s_last) {
         __threadfence();
+        // eight independent loads in flight per thread (a plain strided
+        // loop waits out one L2 round trip per partial); the maximum is
+        // exact, so the order does not matter
         T r = T(0);
-        for (int i = threadIdx.x; i < nslots; i += blockDim.x) {
-            T w = __ldcg(partial + i);
+        const int bd = blockDim.x;
+        int i = threadIdx.x;
+        for (; i + 7 * bd < nslots; i += 8 * bd) {
+            T w[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) w[u] = __ldcg(partial + i + u * bd);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) r = w[u] > r ? w[u] : r;
+        }
+        for (; i < nslots; i += bd) {
+            const T w = __ldcg(partial + i);
             r = w > r ? w : r;
         }
         r = block_max(r);
