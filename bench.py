@@ -56,6 +56,21 @@ MOVED_ARRAYS_PER_STEP = 10
 NCU_TRAFFIC_128 = 8.433e6
 NCU_TRAFFIC_1024 = 8.578e8
 FALLBACK_HBM_GBS = 6800.0
+# FP64 floating-point operations per DOF-stage of the 128^2 p = 3 Euler stage
+# kernel (2 per DFMA, 1 per DMUL / DADD, counted by ncu over the three RK
+# stages; IEEE division and square root are DFMA sequences), and the FP64
+# peak derived from GB300's units: 152 SMs x 2 FP64 FMA per SM per clock x 2
+# flops x 2.07 GHz = 1.26 TFLOP/s (the nominal 1.25).
+FP64_FLOPS_PER_DOF_STAGE = 297.4
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def f64_roofline(rate):
+    if FP64_FLOPS_PER_DOF_STAGE is None:
+        return {"bound": "alu", "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "achieved": None, "frac": None}
+    a = rate * FP64_FLOPS_PER_DOF_STAGE / 1e12
+    return {"bound": "alu", "achieved": a, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": a / FP64_PEAK_TFLOPS, "flops_per_dof_stage": FP64_FLOPS_PER_DOF_STAGE}
 
 
 def parse():
@@ -65,9 +80,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cpr", "reference"], default="cpr")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["vortex128", "vortex1024", "batch", "fv1536", "limited", "radial"],
-                    default="vortex128", help="vortex1024 / batch / fv1536 / limited / radial: only that "
-                    "block (short runs for profiling)")
+    ap.add_argument("--workload", choices=["vortex128", "vortex1024", "batch", "fv1536", "limited", "radial", "f64"],
+                    default="vortex128", help="vortex1024 / batch / fv1536 / limited / radial / f64: "
+                    "only that block (short runs for profiling)")
     ap.add_argument("--no-tune", action="store_true",
                     help="--workload batch: the untuned launch (for profilers, whose serialised replays "
                     "distort the autotuner's timings)")
@@ -165,24 +180,26 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world):
+def _reduce_over_ranks(x, world, op):
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    # NCCL reduces device tensors; gloo (the CPU process groups) host ones
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(x, world):
+    import torch.distributed as dist
+    return _reduce_over_ranks(x, world, dist.ReduceOp.MAX)
 
 
 def sum_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce_over_ranks(x, world, dist.ReduceOp.SUM)
 
 
 # ---------------------------------------------------------------------------
@@ -578,6 +595,30 @@ def run_hbm_only(args):
     print(json.dumps(hbm_case(make, peak, max(1, args.steps))), flush=True)
 
 
+def run_f64_only(args):
+    """FP64 path on the 128^2 p = 3 vortex: `steps` CFL RK3 steps timed after
+    three untimed ones (a short run for profiling the FP64 stage kernel)."""
+    import torch
+    from paper_1709_01619_gb300 import _native as nat
+    from paper_1709_01619_gb300 import inputs
+    cfg = nat.Config(eqn=nat.EULER, nx=NX, ny=NX, p=P, x1=L, y1=L, cfl=CFL, dtype=nat.F64)
+    with nat.Context(cfg) as ctx:
+        x, y = ctx.point_coords()
+        q = torch.tensor(inputs.vortex(x, y, eps=EPS), dtype=torch.float64, device="cuda")
+        ctx.step(q, 3)
+        torch.cuda.synchronize()
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev[0].record()
+        ctx.step(q, args.steps)
+        ev[1].record()
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1])
+    dof = NX * NX * (P + 1) ** 2
+    rate = dof * 3 * args.steps / (ms * 1e-3)
+    print(json.dumps({"workload": "euler_vortex_128x128_p3_fp64", "rk3_steps": args.steps, "ms": ms,
+                      "dof_stage_per_s": rate, **f64_roofline(rate)}), flush=True)
+
+
 def run_cpr(args, world, rank, local):
     import torch
     from paper_1709_01619_gb300 import _native as nat
@@ -710,7 +751,7 @@ def run_cpr(args, world, rank, local):
         "adjoint": adj,
         "paper_setting": paper,
         "f64": {"value": value64, "unit": UNIT, "ms_per_solve": ms64, "rk3_steps": n64,
-                "bound": "alu"},
+                "roofline": f64_roofline(value64)},
         "l2_rho_avg_error": {"f32": err32, "f64": err64},
         "f32_vs_f64_rel_l2": diff,
         "speedup_f32_over_f64": value / world / value64 if value64 > 0 else None,
@@ -737,6 +778,8 @@ def main():
         print(json.dumps(limited_case(peaks()[0], fp64_steps=max(1, args.steps))), flush=True)
     elif args.workload == "radial":
         print(json.dumps(radial_case()), flush=True)
+    elif args.workload == "f64":
+        run_f64_only(args)
     elif args.workload == "fv1536":
         print(json.dumps(fv_case(peaks()[0], fp64_steps=max(1, args.steps))), flush=True)
     else:
