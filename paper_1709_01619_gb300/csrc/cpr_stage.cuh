@@ -265,9 +265,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
     constexpr int N = P + 1, NN = N * N, V = NVars<EQ>::value;
     constexpr int NT = TX * TY * N;
     // Two-lane path (pairs of points of a line; packed FP32 instructions):
-    // even N, LP divergence, fluxes evaluated directly.
-    constexpr bool PAIRED = N % 2 == 0 && DIV == DIV_LP && !DELTA;
-    constexpr int NP = N / 2;
+    // LP divergence, fluxes evaluated directly; even N, and N = 5 in FP32
+    // (FP64 pairs are two scalar operations, so an odd line's last pair
+    // would only add work there; for N = 3 in FP32 it measured 1 % faster on
+    // the batch and 1 % slower on the limited run).  An odd line's last pair
+    // repeats its last point (PH): the table pairs carry zero for it, and
+    // its derivative and residual lanes are not stored.
+    constexpr bool PAIRED = DIV == DIV_LP && !DELTA && (N % 2 == 0 || (sizeof(T) == 4 && N == 5));
+    constexpr int NP = (N + 1) / 2;
+    auto PH = [](int i) { return i < N ? i : N - 1; };
     static_assert(TX * TY >= TX + TY, "every tile-edge face point needs a thread of its own");
     using L = StageLayout<N, V, TX, TY, DELTA>;
     T* sq = reinterpret_cast<T*>(smem_raw);
@@ -334,7 +340,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
 #pragma unroll
-                for (int v = 0; v < V; ++v) qp[j][v] = pmk(d[2 * j][v], d[2 * j + 1][v]);
+                for (int v = 0; v < V; ++v) qp[j][v] = pmk(d[2 * j][v], d[PH(2 * j + 1)][v]);
                 flux_pair<EQ, 0>(qp[j], A.ph, fp[j]);
             }
 #pragma unroll
@@ -355,7 +361,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
 #pragma unroll
                     for (int l = 1; l < N; ++l) r = pfma(tp.D2[i][l], pbc(l % 2 ? cf[l / 2].v.y : cf[l / 2].v.x), r);
                     rx[2 * i][v] = r.v.x;
-                    rx[2 * i + 1][v] = r.v.y;
+                    if (2 * i + 1 < N) rx[2 * i + 1][v] = r.v.y;
                 }
             }
         } else {
@@ -458,7 +464,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
                 if constexpr (PAIRED) {
                     Pr<T> lp2[NP];
 #pragma unroll
-                    for (int j = 0; j < NP; ++j) lp2[j] = pmk(line[2 * j], line[2 * j + 1]);
+                    for (int j = 0; j < NP; ++j) lp2[j] = pmk(line[2 * j], line[PH(2 * j + 1)]);
                     dv = pdot<NP>(side ? tp.lm2 : tp.lp2, lp2);
                 } else {
                     dv = line_dot<N>(coef, line);
@@ -499,7 +505,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
 #pragma unroll
-                for (int v = 0; v < V; ++v) qp[j][v] = pmk(d[2 * j][v], d[2 * j + 1][v]);
+                for (int v = 0; v < V; ++v) qp[j][v] = pmk(d[2 * j][v], d[PH(2 * j + 1)][v]);
                 flux_pair<EQ, 1>(qp[j], A.ph, gp[j]);
             }
 #pragma unroll
@@ -520,7 +526,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
 #pragma unroll
                     for (int l = 1; l < N; ++l) r = pfma(tp.D2[i][l], pbc(l % 2 ? cg[l / 2].v.y : cg[l / 2].v.x), r);
                     ry[2 * i][v] = r.v.x;
-                    ry[2 * i + 1][v] = r.v.y;
+                    if (2 * i + 1 < N) ry[2 * i + 1][v] = r.v.y;
                 }
             }
         } else {
@@ -687,13 +693,14 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
             if constexpr (PAIRED) {
 #pragma unroll
                 for (int i = 0; i < NP; ++i) {
-                    Pr<T> ys = pfma(pmk(jb[2 * i], jb[2 * i + 1]), pbc(glk), pmk(acc[2 * i], acc[2 * i + 1]));
-                    ys = pfma(pmk(jt[2 * i], jt[2 * i + 1]), pbc(grk), ys);
-                    Pr<T> xs = pfma(pbc(JL[v]), tp.dgl2[i], pmk(rx[2 * i][v], rx[2 * i + 1][v]));
+                    const int i1 = PH(2 * i + 1);
+                    Pr<T> ys = pfma(pmk(jb[2 * i], jb[i1]), pbc(glk), pmk(acc[2 * i], acc[i1]));
+                    ys = pfma(pmk(jt[2 * i], jt[i1]), pbc(grk), ys);
+                    Pr<T> xs = pfma(pbc(JL[v]), tp.dgl2[i], pmk(rx[2 * i][v], rx[i1][v]));
                     xs = pfma(pbc(JR), tp.dgr2[i], xs);
                     const Pr<T> r = pfma(pbc(-A.rhx2), xs, pmul(pbc(-A.rhy2), ys));
                     o[2 * i][v] = r.v.x;
-                    o[2 * i + 1][v] = r.v.y;
+                    if (2 * i + 1 < N) o[2 * i + 1][v] = r.v.y;
                 }
             } else {
 #pragma unroll
