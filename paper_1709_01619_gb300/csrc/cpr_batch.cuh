@@ -43,6 +43,7 @@ struct BatchInst {
 template <class T>
 struct BatchArgs {
     const BatchInst<T>* inst;
+    const int* tile_inst;  // work item -> instance of the group
     int ninst, total;  // instances of the group, work items
     int mode;          // stage mode (cpr_common.cuh)
     int swap;          // increment form: the high part of q^n is in Y (else X)
@@ -57,20 +58,16 @@ constexpr int batch_min_blocks()
     return stage_min_blocks<T, N>();
 }
 
-// One work item (tile w of the group's list): thread 0 finds its instance
-// and fills the stage arguments in shared memory, then the CTA runs the tile.
+// One work item (tile w of the group's list): thread 0 looks up its
+// instance (one load from the work-item map, instead of a binary search of
+// dependent loads that the whole CTA would wait out) and fills the stage
+// arguments in shared memory, then the CTA runs the tile.
 template <class T, int P, int EQ, int DIV, int FLUX, int TX, int TY, bool DELTA>
 __device__ __forceinline__ void batch_item(const BatchArgs<T>& B, int w, StageArgs<T>& sA, int& s_t, int& s_n,
                                            unsigned char* smem_raw)
 {
     if (threadIdx.x == 0) {
-        int lo = 0, hi = B.ninst - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (B.inst[mid].tile0 <= w) lo = mid;
-            else hi = mid - 1;
-        }
-        const BatchInst<T>& I = B.inst[lo];
+        const BatchInst<T>& I = B.inst[B.tile_inst[w]];
         StageArgs<T>& A = sA;
         A.npts = I.npts;
         A.nx = I.nx;

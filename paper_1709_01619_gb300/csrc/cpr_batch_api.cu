@@ -34,6 +34,7 @@ struct Group {
     int total[cpr::kBatchFamilies] = {0, 0};  // work items per family
     void* d_inst[cpr::kBatchFamilies] = {nullptr, nullptr};
     void* h_inst[cpr::kBatchFamilies] = {nullptr, nullptr};  // pinned mirrors
+    int* d_map[cpr::kBatchFamilies] = {nullptr, nullptr};     // work item -> instance (member index)
     int fam = 0;                              // chosen tile family
     int grid = 0;                             // chosen grid (= total: one CTA per tile)
     int occ[cpr::kBatchFamilies] = {0, 0};    // resident CTAs per SM
@@ -107,6 +108,7 @@ cudaError_t batch_launch(cpr_batch* b, Group& g, int fam, int grid, int mode, in
 {
     BatchArgs<T> B;
     B.inst = static_cast<const BatchInst<T>*>(g.d_inst[fam]);
+    B.tile_inst = g.d_map[fam];
     B.ninst = (int)g.members.size();
     B.total = g.total[fam];
     B.mode = mode;
@@ -230,6 +232,28 @@ cudaError_t upload_tables(cpr_batch* b, Group& g, cudaStream_t s)
     return cudaSuccess;
 }
 
+// Work item -> instance maps of both tile families (fixed for the batch's
+// lifetime: they depend on the grids only).
+cudaError_t build_tile_maps(cpr_batch* b, Group& g)
+{
+    for (int fam = 0; fam < cpr::kBatchFamilies; ++fam) {
+        int tx, ty;
+        cpr::batch_tile(fam, &tx, &ty);
+        std::vector<int> map;
+        map.reserve(g.total[fam]);
+        for (size_t m = 0; m < g.members.size(); ++m) {
+            const LaunchCfg& lc = b->lcs[g.members[m]];
+            const int nt = ((lc.nx + tx - 1) / tx) * ((lc.ny + ty - 1) / ty);
+            map.insert(map.end(), nt, (int)m);
+        }
+        if ((int)map.size() != g.total[fam]) return cudaErrorInvalidValue;
+        cudaError_t e = cudaMalloc(&g.d_map[fam], sizeof(int) * map.size());
+        if (e == cudaSuccess) e = cudaMemcpy(g.d_map[fam], map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 template <class T>
 cudaError_t group_occupancy(cpr_batch* b, Group& g)
 {
@@ -259,6 +283,7 @@ void free_batch(cpr_batch* b)
     for (Group& g : b->groups)
         for (int f = 0; f < cpr::kBatchFamilies; ++f) {
             cudaFree(g.d_inst[f]);
+            cudaFree(g.d_map[f]);
             if (g.h_inst[f]) cudaFreeHost(g.h_inst[f]);
         }
     cudaFree(b->ctrls);
@@ -370,6 +395,7 @@ extern "C" cpr_status cpr_batch_init(const cpr_config* cfgs, int n, void* stream
             fill_tables<double>(b, g, nullptr);
             e = group_occupancy<double>(b, g);
         }
+        if (e == cudaSuccess) e = build_tile_maps(b, g);
         b->groups.push_back(g);
     }
     if (e != cudaSuccess) {
