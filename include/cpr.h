@@ -259,11 +259,23 @@ cpr_status cpr_batch_step(cpr_batch* b, void* const* q_devs, int nsteps, double 
 /* Autotuner: for each order group, times one RK3 step for each tile family
  * (8x8 and 16x4 elements per CTA) with one CTA per tile and with each
  * persistent grid of 1..max resident CTAs per SM smaller than that, and
- * keeps the fastest.  The states q_devs are not modified and the simulated
- * times are kept.  choices (nullable) receives 3 ints per group: p, family,
- * grid size (equal to the group's tile count for one CTA per tile);
- * *ngroups (nullable) the group count (at most 4).  Synchronises. */
+ * keeps the fastest; then times the whole batch in that grouped form against
+ * the per-instance form (see cpr_batch_set_form) and keeps the faster.  The
+ * states q_devs are not modified and the simulated times are kept.  choices
+ * (nullable) receives 3 ints per group: p, family, grid size (equal to the
+ * group's tile count for one CTA per tile; family 2 and grid 0 when the
+ * per-instance form won); *ngroups (nullable) the group count (at most 4).
+ * Synchronises. */
 cpr_status cpr_batch_tune(cpr_batch* b, void* const* q_devs, int* choices, int* ngroups);
+
+/* Form of the batched step.  0 (the default): one launch per order group
+ * and stage over the work list of all tiles of that order.  1: every
+ * instance runs the single-problem stage kernel on a stream of its own
+ * inside the step graphs (independent chains, joined at the end of a graph;
+ * the state pointers are baked into the graphs, which are re-captured when
+ * they change).  Results are the same to rounding.  Synchronises;
+ * CPR_EINVAL for another value. */
+cpr_status cpr_batch_set_form(cpr_batch* b, int per_instance);
 
 /* Simulated time and steps of instance i (synchronises); set the time of
  * every instance (synchronises). */

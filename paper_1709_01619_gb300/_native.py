@@ -35,7 +35,7 @@ EXPORTS = (
     "cpr_residual", "cpr_step", "cpr_step_host", "cpr_limit", "cpr_get_marks", "cpr_averages",
     "cpr_norms", "cpr_set_time", "cpr_get_time", "cpr_residual_vjp", "cpr_step_vjp",
     "cpr_step_noalloc", "cpr_batch_init", "cpr_batch_destroy", "cpr_batch_last_error",
-    "cpr_batch_step", "cpr_batch_tune", "cpr_batch_get_time", "cpr_batch_set_time",
+    "cpr_batch_step", "cpr_batch_tune", "cpr_batch_set_form", "cpr_batch_get_time", "cpr_batch_set_time",
 )
 
 
@@ -174,6 +174,8 @@ def load():
             lib.cpr_batch_step.argtypes = [P, ctypes.POINTER(P), I, D, D]
             lib.cpr_batch_tune.restype = I
             lib.cpr_batch_tune.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(I), ctypes.POINTER(I)]
+            lib.cpr_batch_set_form.restype = I
+            lib.cpr_batch_set_form.argtypes = [P, I]
             lib.cpr_batch_get_time.restype = I
             lib.cpr_batch_get_time.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(LL)]
             lib.cpr_batch_set_time.restype = I
@@ -377,6 +379,10 @@ class Batch:
         ng = ctypes.c_int()
         self._check(self.lib.cpr_batch_tune(self.h, self._ptrs(qs), choices, ctypes.byref(ng)))
         return [tuple(choices[3 * k:3 * k + 3]) for k in range(ng.value)]
+
+    def set_form(self, per_instance: bool):
+        """Grouped launches (False) or per-instance launch chains (True)."""
+        self._check(self.lib.cpr_batch_set_form(self.h, int(bool(per_instance))))
 
     def get_time(self, i: int):
         t = ctypes.c_double()

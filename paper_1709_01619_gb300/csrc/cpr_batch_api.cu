@@ -23,6 +23,7 @@ using cpr::BatchArgs;
 using cpr::BatchInst;
 using cpr::Ctrl;
 using cpr::LaunchCfg;
+using cpr::StagePtrs;
 
 namespace {
 
@@ -63,6 +64,14 @@ struct cpr_batch {
     std::vector<const void*> x_cached;
     cudaGraphExec_t g1 = nullptr, g2 = nullptr, gK = nullptr;
     bool graphs_valid = false;
+    // per-instance form (chosen by the autotuner): every instance runs the
+    // single-problem stage kernel on a stream of its own inside the graphs,
+    // its arguments in the kernel parameters; the chains join only at the
+    // end of a graph
+    bool per_inst = false;
+    std::vector<cudaStream_t> ist;
+    std::vector<cudaEvent_t> iev;
+    cudaEvent_t fork_ev = nullptr;
     std::string err;
 };
 
@@ -145,8 +154,99 @@ cudaError_t batch_enqueue_step(cpr_batch* b, int swap, cudaStream_t s)
     return batch_stage(b, cpr::MODE_SO3, 0, s);
 }
 
+// One stage of instance i with the single-problem kernel (buffers as in
+// batch_item).
+cudaError_t inst_stage(cpr_batch* b, int i, int mode, int swap, cudaStream_t s)
+{
+    void* X = const_cast<void*>(b->x_cached[i]);
+    void* Y = b->Y[i];
+    void* Z = b->Z[i];
+    void* hiq = swap ? Y : X;
+    void* other = swap ? X : Y;
+    StagePtrs p{};
+    p.lo = b->lo[i];
+    switch (mode) {
+    case cpr::MODE_SO1: p.qs = X; p.out = Y; break;
+    case cpr::MODE_SO2: p.qs = Y; p.qn = X; p.out = Z; break;
+    case cpr::MODE_SO3: p.qs = Z; p.qn = X; p.out = X; break;
+    case cpr::MODE_INC1: p.qs = hiq; p.out = other; break;
+    case cpr::MODE_INC2: p.qs = hiq; p.qb = other; p.out = Z; break;
+    default: p.qs = hiq; p.qb = Z; p.out = other; break;
+    }
+    const bool wave = mode == cpr::MODE_SO3 || mode == cpr::MODE_INC3;
+    return b->dtype == CPR_F32 ? cpr::launch_stage<float>(b->lcs[i], mode, p, wave, s)
+                               : cpr::launch_stage<double>(b->lcs[i], mode, p, wave, s);
+}
+
+cudaError_t ensure_inst_streams(cpr_batch* b)
+{
+    if (!b->ist.empty()) return cudaSuccess;
+    cudaError_t e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+    for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        b->ist.push_back(st);
+        b->iev.push_back(ev);
+    }
+    for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
+        const LaunchCfg& lc = b->lcs[i];
+        e = b->dtype == CPR_F32 ? cpr::prepare_stage<float>(lc) : cpr::prepare_stage<double>(lc);
+    }
+    return e;
+}
+
+// Enqueue on s (which must be capturing) `steps` RK3 steps of every instance
+// as independent chains: fork from s, one stream per instance, join back.
+// timing != 0: only stages 1 and 2 with swap 0 (they leave the caller's
+// states, the low parts and the time control untouched), for the autotuner.
+cudaError_t enqueue_inst_chains(cpr_batch* b, int steps, cudaStream_t s, bool timing)
+{
+    cudaError_t e = cudaEventRecord(b->fork_ev, s);
+    for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
+        cudaStream_t si = b->ist[i];
+        e = cudaStreamWaitEvent(si, b->fork_ev, 0);
+        for (int k = 0; k < steps && e == cudaSuccess; ++k) {
+            if (timing) {
+                e = inst_stage(b, i, b->use_inc ? cpr::MODE_INC1 : cpr::MODE_SO1, 0, si);
+                if (e == cudaSuccess) e = inst_stage(b, i, b->use_inc ? cpr::MODE_INC2 : cpr::MODE_SO2, 0, si);
+            } else if (b->use_inc) {
+                const int sw = k % 2;
+                e = inst_stage(b, i, cpr::MODE_INC1, sw, si);
+                if (e == cudaSuccess) e = inst_stage(b, i, cpr::MODE_INC2, sw, si);
+                if (e == cudaSuccess) e = inst_stage(b, i, cpr::MODE_INC3, sw, si);
+            } else {
+                e = inst_stage(b, i, cpr::MODE_SO1, 0, si);
+                if (e == cudaSuccess) e = inst_stage(b, i, cpr::MODE_SO2, 0, si);
+                if (e == cudaSuccess) e = inst_stage(b, i, cpr::MODE_SO3, 0, si);
+            }
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(b->iev[i], si);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->iev[i], 0);
+    }
+    return e;
+}
+
 cudaError_t batch_capture(cpr_batch* b, int steps, cudaGraphExec_t* exec)
 {
+    if (b->per_inst) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = ensure_inst_streams(b);
+        if (e != cudaSuccess) return e;
+        e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        const cudaError_t ee = enqueue_inst_chains(b, steps, b->cap, false);
+        e = cudaStreamEndCapture(b->cap, &g);
+        if (ee != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return ee;
+        }
+        if (e != cudaSuccess) return e;
+        e = cudaGraphInstantiate(exec, g, 0);
+        cudaGraphDestroy(g);
+        return e;
+    }
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
@@ -290,6 +390,11 @@ void free_batch(cpr_batch* b)
     cudaFree(b->ctrl_backup);
     if (b->h_ctrls) cudaFreeHost(b->h_ctrls);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (cudaStream_t st : b->ist)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->iev)
+        if (ev) cudaEventDestroy(ev);
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
 }
 
 }  // namespace
@@ -450,6 +555,7 @@ static cpr_status batch_bind(cpr_batch* b, void* const* q)
         }
     }
     for (int i = 0; i < b->n; ++i) b->x_cached[i] = q[i];
+    if (b->per_inst) drop_graphs(b);  // their kernel parameters hold the pointers
     return CPR_OK;
 }
 
@@ -504,6 +610,19 @@ extern "C" cpr_status cpr_batch_step(cpr_batch* b, void* const* q, int nsteps, d
     } else {
         for (int k = 0; k < rest; ++k) BATCH_CUDA(b, cudaGraphLaunch(b->g1, b->stream));
     }
+    return CPR_OK;
+}
+
+extern "C" cpr_status cpr_batch_set_form(cpr_batch* b, int per_instance)
+{
+    if (!b) return CPR_EINVAL;
+    if (per_instance != 0 && per_instance != 1) {
+        b->err = "per_instance must be 0 or 1";
+        return CPR_EINVAL;
+    }
+    BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+    b->per_inst = per_instance != 0;
+    drop_graphs(b);
     return CPR_OK;
 }
 
@@ -594,6 +713,48 @@ extern "C" cpr_status cpr_batch_tune(cpr_batch* b, void* const* q, int* choices,
         g.fam = best_fam;
         g.grid = best_grid;
     }
+    // The grouped launches just chosen against per-instance chains (stages 1
+    // and 2 of every instance, each form captured in a graph and timed over
+    // three replays).
+    {
+        auto timed = [&](bool inst, float* ms) -> cudaError_t {
+            cudaGraph_t gr = nullptr;
+            cudaGraphExec_t ex = nullptr;
+            cudaError_t e = inst ? ensure_inst_streams(b) : cudaSuccess;
+            if (e != cudaSuccess) return e;
+            e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return e;
+            cudaError_t ee = cudaSuccess;
+            if (inst) {
+                ee = enqueue_inst_chains(b, 1, b->cap, true);
+            } else {
+                for (int m = 0; m < 2 && ee == cudaSuccess; ++m) {
+                    const int mode = b->use_inc ? modes_inc[m] : modes_so[m];
+                    for (Group& g : b->groups) {
+                        ee = b->dtype == CPR_F32 ? batch_launch<float>(b, g, g.fam, g.grid, mode, 0, b->cap)
+                                                 : batch_launch<double>(b, g, g.fam, g.grid, mode, 0, b->cap);
+                        if (ee != cudaSuccess) break;
+                    }
+                }
+            }
+            e = cudaStreamEndCapture(b->cap, &gr);
+            if (ee == cudaSuccess && e == cudaSuccess) e = cudaGraphInstantiate(&ex, gr, 0);
+            if (gr) cudaGraphDestroy(gr);
+            if (ee != cudaSuccess) e = ee;
+            if (e == cudaSuccess) e = cudaGraphLaunch(ex, b->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = cudaGraphLaunch(ex, b->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+            if (ex) cudaGraphExecDestroy(ex);
+            return e;
+        };
+        float t_grouped = 0.f, t_inst = 0.f;
+        BATCH_CUDA(b, timed(false, &t_grouped));
+        BATCH_CUDA(b, timed(true, &t_inst));
+        b->per_inst = t_inst < t_grouped;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     BATCH_CUDA(b, cudaMemcpyAsync(b->ctrls, b->ctrl_backup, sizeof(Ctrl) * b->n, cudaMemcpyDeviceToDevice,
@@ -604,8 +765,8 @@ extern "C" cpr_status cpr_batch_tune(cpr_batch* b, void* const* q, int* choices,
     if (choices)
         for (size_t k = 0; k < b->groups.size(); ++k) {
             choices[3 * k] = b->groups[k].p;
-            choices[3 * k + 1] = b->groups[k].fam;
-            choices[3 * k + 2] = b->groups[k].grid;
+            choices[3 * k + 1] = b->per_inst ? 2 : b->groups[k].fam;
+            choices[3 * k + 2] = b->per_inst ? 0 : b->groups[k].grid;
         }
     return CPR_OK;
 }

@@ -50,18 +50,42 @@ def singles(cs, q0s, nsteps, dt, t_end=0.0):
     return res, times
 
 
+@pytest.mark.parametrize("per_instance", [False, True])
 @pytest.mark.parametrize("dtype", [nat.F64, nat.F32])
 @pytest.mark.parametrize("nsteps", [1, 2, 5])
-def test_batch_matches_single_contexts(dtype, nsteps):
+def test_batch_matches_single_contexts(dtype, nsteps, per_instance):
+    """Grouped form: the same arithmetic as single contexts up to the
+    kernels' rounding; per-instance form: the single-problem kernels
+    themselves, so the states are equal bit for bit."""
     cs = cfgs(dtype)
     q0s = [initial(c, s[3]) for c, s in zip(cs, SHAPES)]
     ref, _ = singles(cs, q0s, nsteps, 0.004)
     with nat.Batch(cs) as b:
+        b.set_form(per_instance)
         qs = [q.clone() for q in q0s]
         b.step(qs, nsteps, 0.004)
         for i, (q, r) in enumerate(zip(qs, ref)):
             assert rel(q, r) <= TOL[dtype], i
+            if per_instance:
+                assert torch.equal(q, r), i
             assert b.get_time(i)[1] == nsteps
+
+
+def test_per_instance_form_follows_new_state_arrays():
+    """The per-instance graphs hold the state pointers: stepping other
+    arrays re-captures them."""
+    cs = cfgs(nat.F32)
+    q0s = [initial(c, s[3]) for c, s in zip(cs, SHAPES)]
+    ref, _ = singles(cs, q0s, 3, 0.004)
+    with nat.Batch(cs) as b:
+        b.set_form(True)
+        qa = [q.clone() for q in q0s]
+        b.step(qa, 3, 0.004)
+        b.set_time(0.0, 0)
+        qb = [q.clone() for q in q0s]
+        b.step(qb, 3, 0.004)
+        for a, c, r in zip(qa, qb, ref):
+            assert torch.equal(a, r) and torch.equal(c, r)
 
 
 def test_batch_matches_oracle_fp64():
@@ -76,8 +100,9 @@ def test_batch_matches_oracle_fp64():
         assert np.linalg.norm(q.cpu().numpy() - q_or) / np.linalg.norm(q_or) <= 1e-12
 
 
+@pytest.mark.parametrize("per_instance", [False, True])
 @pytest.mark.parametrize("dtype", [nat.F64, nat.F32])
-def test_batch_cfl_steps_per_instance_to_t_end(dtype):
+def test_batch_cfl_steps_per_instance_to_t_end(dtype, per_instance):
     cs = cfgs(dtype)
     # a smooth periodic solution: rounding differences between the two paths
     # are not amplified by the flow (a vortex cut off by the small periodic
@@ -90,6 +115,7 @@ def test_batch_cfl_steps_per_instance_to_t_end(dtype):
     t_end = 0.3
     ref, times = singles(cs, q0s, 200, 0.0, t_end)
     with nat.Batch(cs) as b:
+        b.set_form(per_instance)
         qs = [q.clone() for q in q0s]
         b.step(qs, 200, 0.0, t_end)
         for i in range(len(cs)):
@@ -106,7 +132,9 @@ def test_batch_tune_keeps_states_and_results():
         qs = [q.clone() for q in q0s]
         choices = b.tune(qs)
         assert {p for p, _, _ in choices} == {1, 2, 3, 4}
-        assert all(f in (0, 1) and g >= 1 for _, f, g in choices)
+        # a tile family and grid per group, or family 2 (per-instance form)
+        assert all((f in (0, 1) and g >= 1) or (f == 2 and g == 0) for _, f, g in choices)
+        assert len({f == 2 for _, f, _ in choices}) == 1
         for q, q0 in zip(qs, q0s):
             assert torch.equal(q, q0)
         assert b.get_time(0) == (0.0, 0)
