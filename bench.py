@@ -289,9 +289,9 @@ def batch_case(peak, steps=100, warmup=3, tune=True):
     """64 isentropic-vortex instances (N ~ U{32..256}, p ~ U{2,3,4}, strength
     ~ U[1,5], numpy seed 0) on [0,10]^2 in FP32, advanced together by the
     batched solver with per-instance CFL steps after autotuning (tune=False:
-    the untuned launch, one CTA per tile of the 8x8 family, which is what the
-    autotuner picks on GB300; a profiler's serialised replays would distort
-    its timings)."""
+    the untuned launch, the grouped form with one CTA per tile of the 8x8
+    family, for profilers, whose serialised replays would distort the
+    autotuner's timings)."""
     import torch
     from paper_1709_01619_gb300 import _native as nat
     from paper_1709_01619_gb300 import inputs
