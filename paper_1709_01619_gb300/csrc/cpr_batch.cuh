@@ -79,6 +79,7 @@ __device__ __forceinline__ void batch_item(const BatchArgs<T>& B, int w, StageAr
         A.do_avg = 0;
         A.avg = nullptr;
         A.do_wave = B.mode == MODE_SO3 || B.mode == MODE_INC3;
+        A.pf_lo = 0;
         A.wave = I.wave;
         A.ctrl = I.ctrl;
         A.rhx2 = I.rhx2;

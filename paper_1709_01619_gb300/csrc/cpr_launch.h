@@ -26,6 +26,7 @@ int build_tables(int p, int pts, int corr, HostTab* t);
 struct LaunchCfg {
     int eqn, p, div, flux;  // flux: FLUX_RUSANOV, FLUX_UPWIND or FLUX_ROE
     int fv_order;           // FV schemes (p = 0): MUSCL order, 2 or 3
+    long long l2_bytes;     // L2 size of the device (0: unknown)
     int nx, ny, bcx, bcy;
     long long ne, npts;
     double hx, hy, gamma, ax, ay, tvb_M, lim_eps;
@@ -35,6 +36,16 @@ struct LaunchCfg {
     int* marks;        // limiter marks
     double* partials;  // norms partials
 };
+
+// L2 size of the current device in bytes (0 when it cannot be queried).
+inline long long current_l2_bytes()
+{
+    int dev = 0, l2 = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess)
+        return l2;
+    (void)cudaGetLastError();
+    return 0;
+}
 
 // Element tile of one stage-kernel CTA (compile-time; overridable for tuning
 // sweeps with -DCPR_TILE_X=.. -DCPR_TILE_Y=..).

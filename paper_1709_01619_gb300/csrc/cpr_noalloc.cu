@@ -123,6 +123,7 @@ extern "C" cpr_status cpr_step_noalloc(const cpr_config* cfg, void* q_dev, int n
     lc.tvb_M = cfg->tvb_M;
     lc.lim_eps = cfg->lim_eps;
     lc.ctrl = ctrl;
+    lc.l2_bytes = cpr::current_l2_bytes();
     if (cpr::build_tables(cfg->p, cfg->pts, cfg->corr, &lc.tab) != 0) return CPR_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool f32 = cfg->dtype == CPR_F32;

@@ -64,6 +64,7 @@ struct StageArgs {
     int tiles_x;
     int mode;
     int do_avg, do_wave;
+    int pf_lo;        // mode 6 on states larger than L2: launch the instantiation that prefetches the low part
     T rhx2, rhy2;     // 2/hx, 2/hy
     Phys<T> ph;
     Tab<T> tab;
@@ -258,7 +259,7 @@ constexpr int stage_min_blocks()
 // TX x TY tiles (row-major); threads tid >= NT of a wider CTA only take part
 // in the barriers.  slot / nslots: this tile's entry in the per-CTA partial
 // maxima of the instance (the last tile to finish reduces them).
-template <class T, int P, int EQ, int DIV, int FLUX, int TX, int TY, bool DELTA>
+template <class T, int P, int EQ, int DIV, int FLUX, int TX, int TY, bool DELTA, bool PF = false>
 __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& tb, const TabPr<T>& tp, int tile,
                                            int tid, unsigned char* smem_raw, int slot, int nslots)
 {
@@ -308,6 +309,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
     T rx[N][V];           // d/dxi of the flux differences along row k
     T eL[V], fL[V];       // own left edge state and flux
     Ref<T> rf;            // own reference (delta form)
+    if (PF && valid && k == 0 && (tx & 1) == 0) {
+        // the low part is first read in phase 4, from HBM when the state
+        // does not fit in L2: start it towards L2 now, one prefetch per
+        // 128-byte line (two elements' rows of one variable)
+#pragma unroll
+        for (int v = 0; v < V; ++v) asm volatile("prefetch.global.L2 [%0];" ::"l"(A.lo + v * A.npts + e * NN));
+    }
     if (valid) {
         T d[N][V], q0[V];
 #pragma unroll
@@ -806,13 +814,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
     }
 }
 
-template <class T, int P, int EQ, int DIV, int FLUX, int TX, int TY, bool DELTA>
+// PF: the instantiation for compensated stages whose states exceed L2 (it
+// prefetches the low part; launched only when StageArgs::pf_lo is set).
+template <class T, int P, int EQ, int DIV, int FLUX, int TX, int TY, bool DELTA, bool PF = false>
 __global__ void __launch_bounds__(TX * TY * (P + 1), (stage_min_blocks<T, P + 1>()))
 cpr_stage_kernel(const StageArgs<T> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    stage_tile<T, P, EQ, DIV, FLUX, TX, TY, DELTA>(A, A.tab, A.tp, blockIdx.x, threadIdx.x, smem_raw, blockIdx.x,
-                                                   gridDim.x);
+    stage_tile<T, P, EQ, DIV, FLUX, TX, TY, DELTA, PF>(A, A.tab, A.tp, blockIdx.x, threadIdx.x, smem_raw,
+                                                       blockIdx.x, gridDim.x);
 }
 
 }  // namespace cpr

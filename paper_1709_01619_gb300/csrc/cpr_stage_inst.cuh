@@ -18,8 +18,18 @@ static cudaError_t stage_one(const LaunchCfg& c, const StageArgs<T>& A, int ctas
     constexpr int NT = kTileX * kTileY * N;
     const size_t smem = sizeof(T) * StageLayout<N, V, kTileX, kTileY, stage_delta<T>()>::TOTAL;
     auto kern = cpr_stage_kernel<T, P, EQ, DIV, FLUX, kTileX, kTileY, stage_delta<T>()>;
-    if (prep) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<ctas, NT, smem, s>>>(A);
+    // the prefetching instantiation only where the compensated FP32 stages
+    // run on large states: Euler, LP divergence, Rusanov flux
+    constexpr bool HAS_PF = sizeof(T) == 4 && EQ == EQ_EULER && DIV == DIV_LP && FLUX == FLUX_RUSANOV;
+    auto kern_pf = cpr_stage_kernel<T, P, EQ, DIV, FLUX, kTileX, kTileY, stage_delta<T>(), HAS_PF>;
+    if (prep) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess && HAS_PF)
+            e = cudaFuncSetAttribute(kern_pf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return e;
+    }
+    if (HAS_PF && A.pf_lo) kern_pf<<<ctas, NT, smem, s>>>(A);
+    else kern<<<ctas, NT, smem, s>>>(A);
     return cudaGetLastError();
 }
 
@@ -61,6 +71,9 @@ static StageArgs<T> make_stage_args(const LaunchCfg& c, int mode, const StagePtr
     A.mode = mode;
     A.do_avg = b.avg != nullptr;
     A.do_wave = do_wave;
+    // the five state arrays of the compensated stage exceed L2
+    A.pf_lo = mode == MODE_INC3 && b.lo != nullptr &&
+              (double)c.npts * (c.eqn == EQ_EULER ? 4 : 1) * sizeof(T) * 5.0 > (double)c.l2_bytes;
     A.rhx2 = T(2.0 / c.hx);
     A.rhy2 = T(2.0 / c.hy);
     A.ph.gamma = T(c.gamma);
