@@ -1,9 +1,9 @@
 // cpr_api.cu -- the C ABI of libcpr.so (declared in include/cpr.h).
 //
 // A context owns the operator tables, two stage buffers (q1, q2 of the SSP-RK3
-// scheme, Sec. 4), the element-average buffer of the limiter, the per-CTA
-// partials of the max-speed reduction, the limiter marks, the device control
-// block (simulated time, step size) and the CUDA graphs of the RK loop.
+// scheme, Sec. 4), the element-average buffer of the limiter, the limiter
+// marks, the device control block (simulated time, step size, the running
+// maximum speed of the CFL reduction) and the CUDA graphs of the RK loop.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,7 +34,6 @@ struct cpr_ctx {
     void* q1 = nullptr;
     void* q2 = nullptr;
     void* avg = nullptr;
-    void* wave = nullptr;
     int* marks = nullptr;
     Ctrl* ctrl = nullptr;
     double* partials = nullptr;
@@ -218,7 +217,6 @@ static void free_all(cpr_ctx* c)
     cudaFree(c->q1);
     cudaFree(c->q2);
     cudaFree(c->avg);
-    cudaFree(c->wave);
     cudaFree(c->marks);
     cudaFree(c->ctrl);
     cudaFree(c->partials);
@@ -261,7 +259,6 @@ extern "C" cpr_status cpr_init(const cpr_config* cfg, void* stream, cpr_ctx** ou
     }
     LaunchCfg& lc = c->lc;
 
-    const int ctas = std::max(cpr::stage_ctas(lc), std::max(cpr::aux_ctas(lc), 1024));
     c->norm_blocks = (int)std::min<long long>(1024, std::max<long long>(1, (c->ne + 255) / 256));
     const size_t sbytes = (size_t)c->nstate * c->esize;
     cudaError_t e = cudaSuccess;
@@ -270,7 +267,6 @@ extern "C" cpr_status cpr_init(const cpr_config* cfg, void* stream, cpr_ctx** ou
     c->use_inc = cfg->dtype == CPR_F32 && !cfg->limiter;
     if (e == cudaSuccess && c->use_inc) e = cudaMalloc(&c->lo, sbytes);
     if (e == cudaSuccess) e = cudaMalloc(&c->avg, (size_t)c->V * c->ne * c->esize);
-    if (e == cudaSuccess) e = cudaMalloc(&c->wave, (size_t)ctas * c->esize);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->marks, (size_t)c->ne * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->ctrl, sizeof(Ctrl));
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->partials, (size_t)c->norm_blocks * cpr::kNormVals * 8);
@@ -280,7 +276,6 @@ extern "C" cpr_status cpr_init(const cpr_config* cfg, void* stream, cpr_ctx** ou
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ctrl, 0, sizeof(Ctrl), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->marks, 0, (size_t)c->ne * sizeof(int), c->stream);
     lc.ctrl = c->ctrl;
-    lc.wave = c->wave;
     lc.marks = c->marks;
     lc.partials = c->partials;
     if (e == cudaSuccess)

@@ -16,7 +16,6 @@ struct AuxArgs {
     const T* avg_in;  // limiter: element averages of q
     T* avg_out;       // averages kernel output
     int* marks;       // limiter: marks[e]
-    T* wave;          // per-CTA partial max speed
     Ctrl* ctrl;
     double* partials; // norms: per-CTA FP64 partial results
     long long ne, npts;
@@ -280,7 +279,7 @@ __global__ void __launch_bounds__(LimShape<T, P, EQ>::NT) cpr_limit_kernel(const
             }
         }
         m = block_max<T>(m);
-        last_cta_time_update<T>(m, A.wave, A.ctrl, /*advance=*/true, blockIdx.x, gridDim.x);
+        last_cta_time_update<T>(m, A.ctrl, /*advance=*/true, gridDim.x);
     }
 }
 
@@ -299,7 +298,7 @@ __global__ void __launch_bounds__(256) cpr_wave_kernel(const AuxArgs<T> A)
         m = s > m ? s : m;
     }
     m = block_max<T>(m);
-    last_cta_time_update<T>(m, A.wave, A.ctrl, /*advance=*/false, blockIdx.x, gridDim.x);
+    last_cta_time_update<T>(m, A.ctrl, /*advance=*/false, gridDim.x);
 }
 
 // FP64 norms, pass 1: each CTA reduces a contiguous element range in a fixed

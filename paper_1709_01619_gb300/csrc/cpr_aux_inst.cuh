@@ -19,7 +19,6 @@ static AuxArgs<T> make_aux(const LaunchCfg& c)
     A.avg_in = nullptr;
     A.avg_out = nullptr;
     A.marks = c.marks;
-    A.wave = static_cast<T*>(c.wave);
     A.ctrl = c.ctrl;
     A.partials = c.partials;
     A.ne = c.ne;

@@ -5,8 +5,8 @@
 // is one persistent launch per order present: its CTAs walk the work list of
 // all tiles of all instances of that order (instance-major, each instance's
 // tiles row-major) with a grid stride, and run the same tile body as the
-// single-problem kernel.  Each instance keeps its own time-control block,
-// step size and per-tile partial maxima; the last tile of an instance to
+// single-problem kernel.  Each instance keeps its own time-control block
+// (step size, running maximum speed); the last tile of an instance to
 // finish closes that instance's step.  Tile shape (family) and the number of
 // resident CTAs per SM are chosen by the autotuner (cpr_batch_tune).
 #pragma once
@@ -31,7 +31,6 @@ struct BatchInst {
     T* Y;          // stage buffer / alternate high part
     T* Z;          // stage buffer
     T* lo;         // low part (FP32 increment form)
-    T* wave;       // per-tile partial maxima
     Ctrl* ctrl;
     long long npts;
     int nx, ny, bcx, bcy;
@@ -80,7 +79,6 @@ __device__ __forceinline__ void batch_item(const BatchArgs<T>& B, int w, StageAr
         A.avg = nullptr;
         A.do_wave = B.mode == MODE_SO3 || B.mode == MODE_INC3;
         A.pf_lo = 0;
-        A.wave = I.wave;
         A.ctrl = I.ctrl;
         A.rhx2 = I.rhx2;
         A.rhy2 = I.rhy2;
@@ -102,7 +100,7 @@ __device__ __forceinline__ void batch_item(const BatchArgs<T>& B, int w, StageAr
         s_n = I.ntiles;
     }
     __syncthreads();
-    stage_tile<T, P, EQ, DIV, FLUX, TX, TY, DELTA>(sA, B.tab, B.tp, s_t, threadIdx.x, smem_raw, s_t, s_n);
+    stage_tile<T, P, EQ, DIV, FLUX, TX, TY, DELTA>(sA, B.tab, B.tp, s_t, threadIdx.x, smem_raw, s_n);
 }
 
 // PERSIST: CTAs walk the work list with a grid stride; otherwise the grid

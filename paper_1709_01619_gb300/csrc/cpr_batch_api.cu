@@ -1,9 +1,9 @@
 // cpr_batch_api.cu -- C ABI of the batched solver (include/cpr.h, cpr_batch_*).
 //
 // A batch owns, per instance, two stage buffers, the low part of the state
-// (FP32), the per-tile partial maxima and a time-control block; per order
-// group, the device work-list tables of both tile families; and the CUDA
-// graphs of the RK loop (one persistent launch per order group and stage).
+// (FP32) and a time-control block; per order group, the device work-list
+// tables of both tile families; and the CUDA graphs of the RK loop (one
+// launch per order group and stage, or per-instance launch chains).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -56,7 +56,7 @@ struct cpr_batch {
     std::vector<cpr_config> cfgs;
     std::vector<LaunchCfg> lcs;
     std::vector<long long> nstate;
-    std::vector<void*> Y, Z, lo, wave;
+    std::vector<void*> Y, Z, lo;
     Ctrl* ctrls = nullptr;
     Ctrl* h_ctrls = nullptr;      // pinned
     Ctrl* ctrl_backup = nullptr;  // device, for the autotuner
@@ -300,7 +300,6 @@ void fill_tables(cpr_batch* b, Group& g, const void* const* x)
             I.Y = static_cast<T*>(b->Y[i]);
             I.Z = static_cast<T*>(b->Z[i]);
             I.lo = static_cast<T*>(b->lo[i]);
-            I.wave = static_cast<T*>(b->wave[i]);
             I.ctrl = b->ctrls + i;
             I.npts = lc.npts;
             I.nx = lc.nx;
@@ -379,7 +378,6 @@ void free_batch(cpr_batch* b)
     for (void* p : b->Y) cudaFree(p);
     for (void* p : b->Z) cudaFree(p);
     for (void* p : b->lo) cudaFree(p);
-    for (void* p : b->wave) cudaFree(p);
     for (Group& g : b->groups)
         for (int f = 0; f < cpr::kBatchFamilies; ++f) {
             cudaFree(g.d_inst[f]);
@@ -443,7 +441,6 @@ extern "C" cpr_status cpr_batch_init(const cpr_config* cfgs, int n, void* stream
     b->Y.assign(n, nullptr);
     b->Z.assign(n, nullptr);
     b->lo.assign(n, nullptr);
-    b->wave.assign(n, nullptr);
     const size_t esize = b->dtype == CPR_F32 ? 4 : 8;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -458,17 +455,9 @@ extern "C" cpr_status cpr_batch_init(const cpr_config* cfgs, int n, void* stream
         LaunchCfg& lc = b->lcs[i];
         b->nstate[i] = lc.npts * b->V;
         const size_t bytes = (size_t)b->nstate[i] * esize;
-        int tiles = 0;
-        for (int fam = 0; fam < cpr::kBatchFamilies; ++fam) {
-            int tx, ty;
-            cpr::batch_tile(fam, &tx, &ty);
-            tiles = std::max(tiles, ((lc.nx + tx - 1) / tx) * ((lc.ny + ty - 1) / ty));
-        }
-        tiles = std::max(tiles, 1024);  // also the CFL start pass
         e = cudaMalloc(&b->Y[i], bytes);
         if (e == cudaSuccess) e = cudaMalloc(&b->Z[i], bytes);
         if (e == cudaSuccess && b->use_inc) e = cudaMalloc(&b->lo[i], bytes);
-        if (e == cudaSuccess) e = cudaMalloc(&b->wave[i], (size_t)tiles * esize);
     }
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->ctrls, sizeof(Ctrl) * n);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->ctrl_backup, sizeof(Ctrl) * n);
@@ -477,7 +466,6 @@ extern "C" cpr_status cpr_batch_init(const cpr_config* cfgs, int n, void* stream
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
         b->lcs[i].ctrl = b->ctrls + i;
-        b->lcs[i].wave = b->wave[i];
     }
     // order groups
     for (int p = 1; p <= 4 && e == cudaSuccess; ++p) {

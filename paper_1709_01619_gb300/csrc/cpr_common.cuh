@@ -64,6 +64,8 @@ struct Ctrl {
     int done;          // 1: t reached t_end, stage kernels do no work
     int last;          // 1: the step in flight was shortened to land on t_end
     int parity;        // steps completed in the current cpr_step call, mod 2
+    unsigned long long wmax;  // running maximum speed of the kernel in flight (bits of a
+                              // non-negative double); 0 between kernels
 };
 
 // Physics in the arithmetic type T.

@@ -32,7 +32,6 @@ struct LaunchCfg {
     double hx, hy, gamma, ax, ay, tvb_M, lim_eps;
     HostTab tab;
     Ctrl* ctrl;
-    void* wave;        // per-CTA partial max speeds (state dtype)
     int* marks;        // limiter marks
     double* partials;  // norms partials
 };
@@ -61,9 +60,6 @@ inline int stage_ctas(const LaunchCfg& c)
 {
     return ((c.nx + kTileX - 1) / kTileX) * ((c.ny + kTileY - 1) / kTileY);
 }
-// upper bound on the CTAs of the element-wise passes (at least kAuxElems / 2
-// elements per CTA)
-inline int aux_ctas(const LaunchCfg& c) { return (int)((c.ne + kAuxElems / 2 - 1) / (kAuxElems / 2)); }
 
 // Buffers of one stage launch (see the modes of cpr_stage.cuh): qs the stage
 // input (hi of q^n in the increment modes), qb the increment added to it

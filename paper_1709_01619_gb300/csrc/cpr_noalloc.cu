@@ -48,6 +48,7 @@ __global__ void noalloc_ctrl_init(cpr::Ctrl* c, double dt)
     c->counter = 0;
     c->done = 0;
     c->last = 0;
+    c->wmax = 0ull;
 }
 
 // Device address of the scratch array on the current device.  In host code

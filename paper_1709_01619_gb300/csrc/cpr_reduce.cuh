@@ -69,46 +69,31 @@ __device__ __forceinline__ void ctrl_advance(Ctrl* c, double max_speed)
 }
 
 // Last-CTA reduction of the per-CTA maxima (call with the CTA maximum in m,
-// from all threads of the CTA).  slot: this CTA's (or tile's) entry among
-// nslots partials.  advance: close the step (stage 3) or only set the next
-// step size (start of a run).
+// from all threads of the CTA).  Every CTA folds its maximum into one word
+// of the control block with an integer atomic maximum (non-negative doubles
+// order as their bit patterns, so the result is the exact maximum in any
+// order; a NaN is left out, as a comparison-based maximum leaves it out);
+// the CTA that arrives last reads and clears it and closes the step.
+// advance: close the step (stage 3) or only set the next step size (start
+// of a run).  nslots: the CTAs (or tiles) that report.
 template <class T>
-__device__ __forceinline__ void last_cta_time_update(T m, T* partial, Ctrl* ctrl, bool advance, int slot,
-                                                     int nslots)
+__device__ __forceinline__ void last_cta_time_update(T m, Ctrl* ctrl, bool advance, int nslots)
 {
     __shared__ int s_last;
     if (threadIdx.x == 0) {
-        partial[slot] = m;
+        const double md = (double)m;
+        if (md > 0.0) atomicMax(&ctrl->wmax, (unsigned long long)__double_as_longlong(md));
         __threadfence();
         const unsigned int ticket = atomicAdd(&ctrl->counter, 1u);
         s_last = ticket == (unsigned int)nslots - 1;
     }
     __syncthreads();
-    if (s_last) {
+    if (s_last && threadIdx.x == 0) {
         __threadfence();
-        // eight independent loads in flight per thread (a plain strided
-        // loop waits out one L2 round trip per partial); the maximum is
-        // exact, so the order does not matter
-        T r = T(0);
-        const int bd = blockDim.x;
-        int i = threadIdx.x;
-        for (; i + 7 * bd < nslots; i += 8 * bd) {
-            T w[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) w[u] = __ldcg(partial + i + u * bd);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) r = w[u] > r ? w[u] : r;
-        }
-        for (; i < nslots; i += bd) {
-            const T w = __ldcg(partial + i);
-            r = w > r ? w : r;
-        }
-        r = block_max(r);
-        if (threadIdx.x == 0) {
-            ctrl->counter = 0;
-            if (advance) ctrl_advance(ctrl, (double)r);
-            else ctrl_next_dt(ctrl, (double)r);
-        }
+        const double r = __longlong_as_double((long long)atomicExch(&ctrl->wmax, 0ull));
+        ctrl->counter = 0;
+        if (advance) ctrl_advance(ctrl, r);
+        else ctrl_next_dt(ctrl, r);
     }
 }
 

@@ -56,7 +56,6 @@ struct StageArgs {
     T* out;           // residual, stage state, increment, or hi of q^{n+1}
     T* lo;            // mode 6: low part of q^n, updated in place
     T* avg;           // element averages of out (do_avg)
-    T* wave;          // per-CTA partial max speed (do_wave)
     Ctrl* ctrl;       // time control (mode >= 1)
     long long npts;   // points per variable, ne * N * N
     int nx, ny;
@@ -257,11 +256,11 @@ constexpr int stage_min_blocks()
 
 // One tile of the stage: the work of one CTA.  tile indexes the instance's
 // TX x TY tiles (row-major); threads tid >= NT of a wider CTA only take part
-// in the barriers.  slot / nslots: this tile's entry in the per-CTA partial
-// maxima of the instance (the last tile to finish reduces them).
+// in the barriers.  nslots: the tiles of the instance that report a maximum
+// speed (the last one to finish closes the step).
 template <class T, int P, int EQ, int DIV, int FLUX, int TX, int TY, bool DELTA, bool PF = false>
 __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& tb, const TabPr<T>& tp, int tile,
-                                           int tid, unsigned char* smem_raw, int slot, int nslots)
+                                           int tid, unsigned char* smem_raw, int nslots)
 {
     constexpr int N = P + 1, NN = N * N, V = NVars<EQ>::value;
     constexpr int NT = TX * TY * N;
@@ -810,7 +809,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
             }
         }
         m = block_max<T>(m);
-        last_cta_time_update<T>(m, A.wave, A.ctrl, /*advance=*/true, slot, nslots);
+        last_cta_time_update<T>(m, A.ctrl, /*advance=*/true, nslots);
     }
 }
 
@@ -822,7 +821,7 @@ cpr_stage_kernel(const StageArgs<T> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     stage_tile<T, P, EQ, DIV, FLUX, TX, TY, DELTA, PF>(A, A.tab, A.tp, blockIdx.x, threadIdx.x, smem_raw,
-                                                       blockIdx.x, gridDim.x);
+                                                       gridDim.x);
 }
 
 }  // namespace cpr

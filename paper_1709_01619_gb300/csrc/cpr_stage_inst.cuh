@@ -60,7 +60,6 @@ static StageArgs<T> make_stage_args(const LaunchCfg& c, int mode, const StagePtr
     A.out = static_cast<T*>(b.out);
     A.lo = static_cast<T*>(b.lo);
     A.avg = static_cast<T*>(b.avg);
-    A.wave = static_cast<T*>(c.wave);
     A.ctrl = c.ctrl;
     A.npts = c.npts;
     A.nx = c.nx;
