@@ -53,8 +53,8 @@ MOVED_ARRAYS_PER_STEP = 10
 # DRAM bytes (read + write) per stage launch, mean over the three RK stages,
 # from ncu captures of the stage kernel as it stands (profiles/): the
 # 128^2 workload replayed cold (writes stay in L2) and the 1024^2 case.
-NCU_TRAFFIC_128 = 8.437e6
-NCU_TRAFFIC_1024 = 8.557e8
+NCU_TRAFFIC_128 = 8.430e6
+NCU_TRAFFIC_1024 = 8.573e8
 FALLBACK_HBM_GBS = 6800.0
 # FP64 floating-point operations per DOF-stage of the 128^2 p = 3 Euler stage
 # kernel (2 per DFMA, 1 per DMUL / DADD, counted by ncu over the three RK
