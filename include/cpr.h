@@ -244,8 +244,8 @@ cpr_status cpr_step_vjp(cpr_ctx* ctx, const void* q_dev, const void* qbar_out_de
 typedef struct cpr_batch cpr_batch;
 
 /* Create a batch of n instances (cfgs[0..n-1]) on the current device; the
- * batch owns two stage buffers, the low part of the state (FP32), partial
- * maxima and a control block per instance. */
+ * batch owns two stage buffers, the low part of the state (FP32) and a
+ * control block per instance. */
 cpr_status cpr_batch_init(const cpr_config* cfgs, int n, void* stream, cpr_batch** out);
 void cpr_batch_destroy(cpr_batch* b);
 const char* cpr_batch_last_error(const cpr_batch* b);
