@@ -20,10 +20,10 @@ class CPRRollout(torch.autograd.Function):
     def forward(ctx, q0, solver: Context, nsteps: int, dt: float, every: int):
         q = q0.detach().contiguous().clone()
         ckpts = []
-        for s in range(nsteps):
-            if s % every == 0:
-                ckpts.append(q.clone())
-            solver.step(q, 1, dt)
+        for s in range(0, nsteps, every):
+            ckpts.append(q.clone())
+            # a segment in one call: the step graphs run back to back
+            solver.step(q, min(every, nsteps - s), dt)
         ctx.solver, ctx.nsteps, ctx.dt, ctx.every, ctx.ckpts = solver, nsteps, dt, every, ckpts
         return q
 
@@ -54,17 +54,29 @@ def rollout(q0, solver: Context, nsteps: int, dt: float, every: int = 20):
     return CPRRollout.apply(q0, solver, int(nsteps), float(dt), int(every))
 
 
+def point_weights(n: int, lobatto: bool):
+    """Quadrature weights of the n solution points on [-1, 1]: the Gauss rule,
+    or the Gauss-Lobatto rule 2 / (n (n - 1) P_{n-1}(x)^2) at its nodes (the
+    ends and the roots of P'_{n-1}), from numpy's Legendre module."""
+    import numpy as np
+    if not lobatto or n < 2:
+        return np.polynomial.legendre.leggauss(n)[1]
+    pn1 = np.polynomial.legendre.Legendre.basis(n - 1)
+    xi = np.concatenate(([-1.0], np.sort(pn1.deriv().roots().real), [1.0]))
+    return 2.0 / (n * (n - 1) * pn1(xi) ** 2)
+
+
 def quadrature_weights(solver: Context) -> torch.Tensor:
     """(hx hy / 4) w_a w_b at every solution point, broadcast over variables:
-    the weights of the L2 misfit J = 1/2 sum W (q - q_target)^2."""
+    the weights of the L2 misfit J = 1/2 sum W (q - q_target)^2, w the
+    quadrature weights of the configuration's solution points."""
     import numpy as np
+    from ._native import LOBATTO
     c = solver.cfg
     n = c.p + 1
-    x, y = solver.point_coords()
     hx, hy = (c.x1 - c.x0) / c.nx, (c.y1 - c.y0) / c.ny
-    # quadrature weights from the points of one element: the Gauss rule of
-    # the reference interval, recovered from numpy's Legendre module
-    xi, w = np.polynomial.legendre.leggauss(n)
+    w = point_weights(n, c.pts == LOBATTO)
     W2 = (hx * hy / 4.0) * np.outer(w, w).reshape(n * n)  # [b, a]
     W = np.broadcast_to(W2, (c.nvars, c.ne, n * n))
-    return torch.tensor(np.ascontiguousarray(W), dtype=c.torch_dtype, device="cuda")
+    return torch.tensor(np.ascontiguousarray(W), dtype=c.torch_dtype,
+                        device="cuda" if torch.cuda.is_available() else "cpu")
