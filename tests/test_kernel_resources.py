@@ -1,0 +1,59 @@
+"""Register budget of the hot FP32 stage kernel, checked at build time (no
+GPU): the Euler / LP / Rusanov stage kernel of p = 3, both instantiations
+(plain and low-part prefetch), must fit the 64 registers that let four
+256-thread CTAs share an SM, without spilling.  A regression here costs a
+quarter of the resident warps or adds local-memory traffic to every launch.
+The figures come from ptxas's resource report (-Xptxas -v)."""
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1709_01619_gb300", "csrc")
+
+
+def _nvcc():
+    for cand in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    return None
+
+
+def ptxas_report(src, tmp_path):
+    nvcc = _nvcc()
+    if nvcc is None:
+        pytest.skip("nvcc not available")
+    cmd = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
+           "-I", CSRC, "-I", os.path.join(ROOT, "include"), "-Xptxas", "-v", "-c", os.path.join(CSRC, src),
+           "-o", str(tmp_path / "k.o")]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    report, current = {}, None
+    for line in r.stderr.splitlines():
+        m = re.search(r"Compiling entry function '(\S+)'", line)
+        if m:
+            current = m.group(1)
+            report[current] = {}
+            continue
+        if current is None:
+            continue
+        m = re.search(r"(\d+) bytes spill stores, (\d+) bytes spill loads", line)
+        if m:
+            report[current]["spill"] = int(m.group(1)) + int(m.group(2))
+        m = re.search(r"Used (\d+) registers", line)
+        if m:
+            report[current]["regs"] = int(m.group(1))
+    return report
+
+
+def test_p3_fp32_stage_kernel_fits_four_ctas_without_spills(tmp_path):
+    report = ptxas_report("cpr_stage_f32_p3.cu", tmp_path)
+    # cpr_stage_kernel<float, 3, EULER, DIV_LP, FLUX_RUSANOV, 8, 8, false, PF>
+    hot = [k for k in report if k.startswith("_ZN3cpr16cpr_stage_kernelIfLi3ELi1ELi0ELi0ELi8ELi8ELb0E")]
+    assert len(hot) == 2, sorted(report)
+    for k in hot:
+        assert report[k]["regs"] <= 64, (k, report[k])
+        assert report[k]["spill"] == 0, (k, report[k])
