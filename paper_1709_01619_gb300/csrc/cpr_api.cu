@@ -51,7 +51,7 @@ struct cpr_ctx {
 };
 
 static thread_local std::string g_init_err;
-static const int kStepsPerGraph = 8;
+static const int kStepsPerGraph = 32;
 
 #define CPR_CUDA(ctx, call)                                                                   \
     do {                                                                                      \

@@ -175,7 +175,7 @@ def test_config2_fixed_steps(dtype):
     q0 = inputs.vortex(x, y, eps=5.0)
     if dtype == nat.F32:
         q0 = q0.astype(np.float32).astype(np.float64)
-    nsteps = 12
+    nsteps = 35  # one 32-step graph, then a two-step and a one-step graph
     q_or, n_or, t_or = oracle.run(o, q0, nsteps)
     with nat.Context(c) as ctx:
         qd = to_dev(q0, c)
@@ -203,12 +203,13 @@ def test_cfl_steps_land_on_t_end():
     assert rel_l2(q, q_or) <= TOL64
 
 
-@pytest.mark.parametrize("nsteps", [1, 2, 3, 7, 8, 9, 17])
+@pytest.mark.parametrize("nsteps", [1, 2, 3, 7, 8, 9, 17, 31, 32, 33, 66])
 def test_fp32_increment_form_step_counts(nsteps):
     """FP32 runs without the limiter use the increment form of SSP-RK3 with a
     compensated state whose high part alternates between two buffers: every
-    step count, odd or even, around the 8-step graph, lands in the caller's
-    array and matches the FP64 oracle."""
+    step count, odd or even, below, at and past the 32-step graph (the rest
+    runs as two-step and one-step graphs), lands in the caller's array and
+    matches the FP64 oracle."""
     c, o = make(dtype=nat.F32, eqn=nat.EULER, nx=19, ny=13, p=3, x1=10.0, y1=7.0, cfl=0.08)
     x, y = oracle.point_coords(o)
     q0 = inputs.vortex(x, y, eps=5.0, xc=5.0, yc=3.5, ly=7.0).astype(np.float32).astype(np.float64)
