@@ -165,6 +165,7 @@ bool cpr_fill_launch_cfg(const cpr_config* cfg, LaunchCfg* out)
     lc.lim_eps = cfg->lim_eps;
     lc.fv_order = cfg->scheme == CPR_SCHEME_FV_MUSCL3 ? 3 : 2;
     lc.l2_bytes = cpr::current_l2_bytes();
+    lc.sms = cpr::current_sm_count();
     if (cpr::build_tables(cfg->p, cfg->pts, cfg->corr, &lc.tab) != 0) return false;
     *out = lc;
     return true;

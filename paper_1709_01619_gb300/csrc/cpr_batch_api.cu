@@ -453,6 +453,10 @@ extern "C" cpr_status cpr_batch_init(const cpr_config* cfgs, int n, void* stream
             return CPR_EINVAL;
         }
         LaunchCfg& lc = b->lcs[i];
+        // instances share the SMs: keep the stage kernel that four CTAs of
+        // any instances can share (the two-CTA instantiation in per-instance
+        // chains measured slower on 64 ragged instances)
+        lc.sms = 0;
         b->nstate[i] = lc.npts * b->V;
         const size_t bytes = (size_t)b->nstate[i] * esize;
         e = cudaMalloc(&b->Y[i], bytes);

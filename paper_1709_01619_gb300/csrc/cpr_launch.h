@@ -27,6 +27,8 @@ struct LaunchCfg {
     int eqn, p, div, flux;  // flux: FLUX_RUSANOV, FLUX_UPWIND or FLUX_ROE
     int fv_order;           // FV schemes (p = 0): MUSCL order, 2 or 3
     long long l2_bytes;     // L2 size of the device (0: unknown)
+    int sms;                // SMs of the device: a stage launch of at most two CTAs per SM takes
+                            // the instantiation compiled for two resident CTAs (0: never)
     int nx, ny, bcx, bcy;
     long long ne, npts;
     double hx, hy, gamma, ax, ay, tvb_M, lim_eps;
@@ -35,6 +37,16 @@ struct LaunchCfg {
     int* marks;        // limiter marks
     double* partials;  // norms partials
 };
+
+// SM count of the current device (0 when it cannot be queried).
+inline int current_sm_count()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+        return n;
+    (void)cudaGetLastError();
+    return 0;
+}
 
 // L2 size of the current device in bytes (0 when it cannot be queried).
 inline long long current_l2_bytes()

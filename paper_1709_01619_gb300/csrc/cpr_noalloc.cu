@@ -125,6 +125,7 @@ extern "C" cpr_status cpr_step_noalloc(const cpr_config* cfg, void* q_dev, int n
     lc.lim_eps = cfg->lim_eps;
     lc.ctrl = ctrl;
     lc.l2_bytes = cpr::current_l2_bytes();
+    lc.sms = cpr::current_sm_count();
     if (cpr::build_tables(cfg->p, cfg->pts, cfg->corr, &lc.tab) != 0) return CPR_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool f32 = cfg->dtype == CPR_F32;

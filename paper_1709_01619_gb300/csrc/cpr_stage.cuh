@@ -324,10 +324,19 @@ constexpr bool stage_delta()
 #ifndef CPR_STAGE_MINB_FP32_N5
 #define CPR_STAGE_MINB_FP32_N5 3
 #endif
-template <class T, int N>
+// Launches of at most two CTAs per SM (grids that fit the device at once,
+// e.g. 128 x 128 elements of p = 3 on 152 SMs) take an instantiation
+// compiled for two resident CTAs: twice the registers let the compiler keep
+// more loads in flight, which is what bounds a CTA when the SM holds only
+// one or two of them.
+#ifndef CPR_STAGE_MINB_WIDE
+#define CPR_STAGE_MINB_WIDE 2
+#endif
+template <class T, int N, bool WIDE = false>
 constexpr int stage_min_blocks()
 {
     return sizeof(T) == 8 ? 1
+           : WIDE         ? CPR_STAGE_MINB_WIDE
                           : (N == 2 ? CPR_STAGE_MINB_FP32_N2
                                     : (N == 3 ? CPR_STAGE_MINB_FP32_N3 : (N == 4 ? CPR_STAGE_MINB_FP32 : CPR_STAGE_MINB_FP32_N5)));
 }
@@ -853,8 +862,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
 
 // PF: the instantiation for compensated stages whose states exceed L2 (it
 // prefetches the low part; launched only when StageArgs::pf_lo is set).
-template <class T, int P, int EQ, int DIV, int FLUX, int TX, int TY, bool DELTA, bool PF = false>
-__global__ void __launch_bounds__(TX * TY * (P + 1), (stage_min_blocks<T, P + 1>()))
+template <class T, int P, int EQ, int DIV, int FLUX, int TX, int TY, bool DELTA, bool PF = false, bool WIDE = false>
+__global__ void __launch_bounds__(TX * TY * (P + 1), (stage_min_blocks<T, P + 1, WIDE>()))
 cpr_stage_kernel(const StageArgs<T> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -112,6 +112,24 @@ def test_residual_parity_fp32(case):
     assert rel_l2(R, R_or) <= TOL32
 
 
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_fp32_residual_on_both_sides_of_the_two_ctas_per_sm_grid(p):
+    """The FP32 Euler / LP / Rusanov stage kernel has an instantiation for
+    grids of at most two 8x8-element CTAs per SM (more registers) and one for
+    larger grids: a grid just past that bound and a small one both match the
+    oracle."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ty = 2 * sms // 24 + 2
+    assert 24 * ty > 2 * sms
+    for nx, ny in ((19, 13), (8 * 24, 8 * ty - 3)):
+        c, o = make(dtype=nat.F32, eqn=nat.EULER, nx=nx, ny=ny, p=p, x1=10.0, y1=10.0 * ny / nx)
+        q = rough_state(o, 4, noise=0.05).astype(np.float32).astype(np.float64)
+        R_or = oracle.residual(o, q)
+        with nat.Context(c) as ctx:
+            R = host(ctx.residual(to_dev(q, c)))
+        assert rel_l2(R, R_or) <= TOL32, (nx, ny)
+
+
 @pytest.mark.parametrize("shape", [(1, 1), (1, 5), (5, 1), (8, 8), (9, 17), (16, 3)])
 def test_residual_degenerate_and_tile_edge_grids(shape):
     for bc in (0, 1):

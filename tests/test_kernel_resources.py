@@ -1,7 +1,8 @@
 """Register budget of the hot FP32 stage kernel, checked at build time (no
-GPU): the Euler / LP / Rusanov stage kernel of p = 3, both instantiations
-(plain and low-part prefetch), must fit the 64 registers that let four
-256-thread CTAs share an SM, without spilling.  A regression here costs a
+GPU): the Euler / LP / Rusanov stage kernel of p = 3, in the two
+instantiations that large grids take (plain and low-part prefetch), must fit
+the 64 registers that let four 256-thread CTAs share an SM, without spilling;
+the one for grids of at most two CTAs per SM must not spill either.  A regression here costs a
 quarter of the resident warps or adds local-memory traffic to every launch.
 The figures come from ptxas's resource report (-Xptxas -v)."""
 import os
@@ -51,9 +52,14 @@ def ptxas_report(src, tmp_path):
 
 def test_p3_fp32_stage_kernel_fits_four_ctas_without_spills(tmp_path):
     report = ptxas_report("cpr_stage_f32_p3.cu", tmp_path)
-    # cpr_stage_kernel<float, 3, EULER, DIV_LP, FLUX_RUSANOV, 8, 8, false, PF>
-    hot = [k for k in report if k.startswith("_ZN3cpr16cpr_stage_kernelIfLi3ELi1ELi0ELi0ELi8ELi8ELb0E")]
-    assert len(hot) == 2, sorted(report)
-    for k in hot:
-        assert report[k]["regs"] <= 64, (k, report[k])
-        assert report[k]["spill"] == 0, (k, report[k])
+    # cpr_stage_kernel<float, 3, EULER, DIV_LP, FLUX_RUSANOV, 8, 8, false, PF, WIDE>
+    pre = "_ZN3cpr16cpr_stage_kernelIfLi3ELi1ELi0ELi0ELi8ELi8ELb0E"
+    hot = {k[len(pre):len(pre) + 12]: report[k] for k in report if k.startswith(pre)}
+    assert sorted(hot) == ["Lb0ELb0EEEvN", "Lb0ELb1EEEvN", "Lb1ELb0EEEvN"], sorted(report)
+    for variant in ("Lb0ELb0EEEvN", "Lb1ELb0EEEvN"):  # plain, low-part prefetch
+        assert hot[variant]["regs"] <= 64, (variant, hot[variant])
+        assert hot[variant]["spill"] == 0, (variant, hot[variant])
+    # the instantiation for grids of at most two CTAs per SM: 256 threads,
+    # two CTAs, so up to 128 registers, and no spills
+    wide = hot["Lb0ELb1EEEvN"]
+    assert wide["regs"] <= 128 and wide["spill"] == 0, wide
