@@ -750,7 +750,7 @@ def run_cpr(args, world, rank, local):
                    "replicas": world},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": NCU_TRAFFIC_128, "peak_source": peak_kind,
-                     "kernel": "cpr_stage_kernel<float,3,Euler,LP,Rusanov>",
+                     "kernel": "cpr_stage_kernel<float,3,Euler,LP,Rusanov> (two-CTA-per-SM instantiation)",
                      "bytes_per_launch": bytes_per_launch,
                      "note": "state (4.2 MB) is L2-resident at this size; traffic from a cold ncu replay"},
         "roofline_hbm_case": hbm,
