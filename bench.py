@@ -53,7 +53,7 @@ MOVED_ARRAYS_PER_STEP = 10
 # DRAM bytes (read + write) per stage launch, mean over the three RK stages,
 # from ncu captures of the stage kernel as it stands (profiles/): the
 # 128^2 workload replayed cold (writes stay in L2) and the 1024^2 case.
-NCU_TRAFFIC_128 = 8.430e6
+NCU_TRAFFIC_128 = 8.429e6
 NCU_TRAFFIC_1024 = 8.573e8
 FALLBACK_HBM_GBS = 6800.0
 # FP64 floating-point operations per DOF-stage of the 128^2 p = 3 Euler stage
