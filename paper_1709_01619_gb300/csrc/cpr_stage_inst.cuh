@@ -22,18 +22,20 @@ static cudaError_t stage_one(const LaunchCfg& c, const StageArgs<T>& A, int ctas
     // run on large states: Euler, LP divergence, Rusanov flux
     constexpr bool HAS_PF = sizeof(T) == 4 && EQ == EQ_EULER && DIV == DIV_LP && FLUX == FLUX_RUSANOV;
     auto kern_pf = cpr_stage_kernel<T, P, EQ, DIV, FLUX, kTileX, kTileY, stage_delta<T>(), HAS_PF>;
-    // and the one for grids of at most two CTAs per SM (same set)
-    auto kern_w = cpr_stage_kernel<T, P, EQ, DIV, FLUX, kTileX, kTileY, stage_delta<T>(), false, HAS_PF>;
+    // and the one for grids of at most two CTAs per SM: FP32 Euler, every
+    // divergence and flux
+    constexpr bool HAS_WIDE = sizeof(T) == 4 && EQ == EQ_EULER;
+    auto kern_w = cpr_stage_kernel<T, P, EQ, DIV, FLUX, kTileX, kTileY, stage_delta<T>(), false, HAS_WIDE>;
     if (prep) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess && HAS_PF)
             e = cudaFuncSetAttribute(kern_pf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess && HAS_PF)
+        if (e == cudaSuccess && HAS_WIDE)
             e = cudaFuncSetAttribute(kern_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         return e;
     }
     if (HAS_PF && A.pf_lo) kern_pf<<<ctas, NT, smem, s>>>(A);
-    else if (HAS_PF && c.sms > 0 && ctas <= 2 * c.sms) kern_w<<<ctas, NT, smem, s>>>(A);
+    else if (HAS_WIDE && c.sms > 0 && ctas <= 2 * c.sms) kern_w<<<ctas, NT, smem, s>>>(A);
     else kern<<<ctas, NT, smem, s>>>(A);
     return cudaGetLastError();
 }
