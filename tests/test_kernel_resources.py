@@ -5,10 +5,12 @@ the 64 registers that let four 256-thread CTAs share an SM, without spilling;
 the one for grids of at most two CTAs per SM must not spill either.  A regression here costs a
 quarter of the resident warps or adds local-memory traffic to every launch.
 The figures come from ptxas's resource report (-Xptxas -v)."""
+import functools
 import os
 import re
 import shutil
 import subprocess
+import tempfile
 
 import pytest
 
@@ -23,14 +25,17 @@ def _nvcc():
     return None
 
 
-def ptxas_report(src, tmp_path):
+@functools.lru_cache(maxsize=None)
+def ptxas_report(src):
+    """{entry: {"regs": n, "spill": bytes}} of one translation unit."""
     nvcc = _nvcc()
     if nvcc is None:
         pytest.skip("nvcc not available")
-    cmd = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
-           "-I", CSRC, "-I", os.path.join(ROOT, "include"), "-Xptxas", "-v", "-c", os.path.join(CSRC, src),
-           "-o", str(tmp_path / "k.o")]
-    r = subprocess.run(cmd, capture_output=True, text=True)
+    with tempfile.TemporaryDirectory() as tmp:
+        cmd = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
+               "-I", CSRC, "-I", os.path.join(ROOT, "include"), "-Xptxas", "-v", "-c", os.path.join(CSRC, src),
+               "-o", os.path.join(tmp, "k.o")]
+        r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     report, current = {}, None
     for line in r.stderr.splitlines():
@@ -50,8 +55,8 @@ def ptxas_report(src, tmp_path):
     return report
 
 
-def test_p3_fp32_stage_kernel_fits_four_ctas_without_spills(tmp_path):
-    report = ptxas_report("cpr_stage_f32_p3.cu", tmp_path)
+def test_p3_fp32_stage_kernel_fits_four_ctas_without_spills():
+    report = ptxas_report("cpr_stage_f32_p3.cu")
     # cpr_stage_kernel<float, 3, EULER, DIV_LP, FLUX_RUSANOV, 8, 8, false, PF, WIDE>
     pre = "_ZN3cpr16cpr_stage_kernelIfLi3ELi1ELi0ELi0ELi8ELi8ELb0E"
     hot = {k[len(pre):len(pre) + 12]: report[k] for k in report if k.startswith(pre)}
@@ -63,3 +68,16 @@ def test_p3_fp32_stage_kernel_fits_four_ctas_without_spills(tmp_path):
     # two CTAs, so up to 128 registers, and no spills
     wide = hot["Lb0ELb1EEEvN"]
     assert wide["regs"] <= 128 and wide["spill"] == 0, wide
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_two_cta_instantiations_do_not_spill(p):
+    """The FP32 Euler stage kernels compiled for grids of at most two CTAs per
+    SM (every divergence and flux) exist for every order and keep all their
+    state in registers."""
+    report = ptxas_report(f"cpr_stage_f32_p{p}.cu")
+    pre = f"_ZN3cpr16cpr_stage_kernelIfLi{p}ELi1E"
+    wide = {k: v for k, v in report.items() if k.startswith(pre) and k.endswith("Lb0ELb0ELb1EEEvNS_9StageArgsIT_EE")}
+    assert len(wide) == 4, sorted(report)  # LP / chain rule x Rusanov / Roe
+    for k, v in wide.items():
+        assert v["spill"] == 0, (k, v)
