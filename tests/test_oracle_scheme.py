@@ -197,6 +197,25 @@ def test_dt_formula_freestream(orc):
     assert orc.dt(cfg, q) == pytest.approx(0.3 * 0.4 / speed, rel=1e-14)
 
 
+def test_max_wave_is_the_maximum_over_every_solution_point(orc):
+    """The CFL speed (Eq. 36) is the largest |V| + c over all solution
+    points, not over element averages: a brute-force maximum over the state
+    array, with one point of one element made the fastest."""
+    cfg = orc.Config(eqn=orc.EULER, nx=5, ny=4, p=3, x1=2.5, y1=2.0, cfl=0.2)
+    x, y = orc.point_coords(cfg)
+    q = inputs.perturbed(inputs.vortex(x, y, eps=2.0, xc=1.25, yc=1.0, lx=2.5, ly=2.0), 11, 0.02)
+    q = np.array(q, dtype=np.float64).reshape(cfg.shape)
+    # one point of one element set to a fast state (rho, u, v, p) = (1, 4, 0.3, 1)
+    q[:, 13, 6] = [1.0, 4.0, 0.3, 1.0 / 0.4 + 0.5 * (16.0 + 0.09)]
+    rho, mx, my, E = q
+    u, v = mx / rho, my / rho
+    p = 0.4 * (E - 0.5 * rho * (u * u + v * v))
+    brute = np.max(np.sqrt(u * u + v * v) + np.sqrt(1.4 * p / rho))
+    assert np.argmax(np.sqrt(u * u + v * v) + np.sqrt(1.4 * p / rho)) == 13 * 16 + 6
+    assert orc.max_wave(cfg, q) == pytest.approx(brute, rel=1e-14)
+    assert orc.dt(cfg, q) == pytest.approx(0.2 * 0.5 / brute, rel=1e-14)
+
+
 # --------------------------------------------------------------------------
 # the paper's tables (loose pins; see the readings in the design notes)
 # --------------------------------------------------------------------------
