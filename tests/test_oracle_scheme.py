@@ -175,6 +175,36 @@ def test_conservation_with_limiter(orc):
     assert orc.norms(cfg, qT)["n_nonphys"] == 0
 
 
+def test_conservation_over_a_thousand_limited_steps(orc):
+    """Periodic LP CPR with the limiter acting after every stage: the sum of
+    the element averages, formed here with numpy's Gauss weights from the
+    point values (not by the oracle), stays constant over 1000 SSP-RK3 steps
+    while the waves of a discontinuous start cross the periodic boundaries.
+    M = 0 (plain minmod test): on a grid this coarse the TVB bound M h^2
+    with the workload's M = 50 would exceed every jump and switch the
+    limiter off, and the unlimited scheme loses positivity."""
+    p = 2
+    cfg = orc.Config(eqn=orc.EULER, nx=10, ny=10, p=p, x0=-1, x1=1, y0=-1, y1=1, cfl=0.1,
+                     limiter=1, tvb_M=0.0, lim_eps=1e-3)
+    x, y = orc.point_coords(cfg)
+    q = np.asarray(inputs.radial_shock(x, y), dtype=np.float64).reshape(cfg.shape)
+    _, w = np.polynomial.legendre.leggauss(p + 1)
+    W = np.outer(w, w).ravel() / 4.0  # point b*n + a gets w_b w_a / 4
+
+    def total(state):
+        return (np.asarray(state).reshape(cfg.shape) * W).sum(axis=(1, 2))
+
+    s0 = total(q)
+    _, marks0, _, _ = orc.limit(cfg, q)
+    qT, n, t = orc.run(cfg, q, 1000)
+    assert n == 1000 and t > 1.0  # long enough for the waves to wrap around
+    # round-off only: about 1e-16 per point and stage, summed as a random walk
+    # over 900 points and 3000 stages gives ~2e-13
+    np.testing.assert_allclose(total(qT), s0, rtol=1e-12, atol=1e-12)
+    assert marks0.sum() > 0
+    assert orc.norms(cfg, qT)["n_nonphys"] == 0
+
+
 def test_rk3_is_third_order_taylor_polynomial(orc):
     """For the linear advection operator R(q) = A q, one SSP-RK3 step must equal
     (I + dt A + dt^2 A^2 / 2 + dt^3 A^3 / 6) q."""
