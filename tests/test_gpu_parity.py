@@ -183,6 +183,41 @@ def test_config1_full_run_fp64():
     assert e_gpu == pytest.approx(e_or, rel=1e-9)
 
 
+def test_config1_full_run_fp32():
+    """The same advection run in FP32 (compensated increment form): all 227
+    steps against the FP64 oracle within the FP32 bound."""
+    c, o = make(dtype=nat.F32, eqn=nat.ADVECTION, nx=16, ny=16, p=2, flux=nat.UPWIND, ax=1.0, ay=1.0,
+                cfl=0.1)
+    x, y = oracle.point_coords(o)
+    q0 = inputs.advection_sine(x, y).astype(np.float32).astype(np.float64)
+    n = 227
+    q_or, _, _ = oracle.run(o, q0, n, 1.0 / n)
+    with nat.Context(c) as ctx:
+        qd = to_dev(q0, c)
+        ctx.step(qd, n, 1.0 / n)
+        q = host(qd)
+        assert ctx.get_time()[1] == n
+    assert rel_l2(q, q_or) <= TOL32
+
+
+def test_fp32_euler_two_hundred_cfl_steps():
+    """Euler vortex on a ragged 19 x 13 grid, p = 3, 200 CFL steps in FP32
+    against the FP64 oracle (the step sizes are the device's own, from its
+    FP64 reduction of the FP32 state, so the two runs also agree in time)."""
+    c, o = make(dtype=nat.F32, eqn=nat.EULER, nx=19, ny=13, p=3, x1=10.0, y1=7.0, cfl=0.08)
+    x, y = oracle.point_coords(o)
+    q0 = inputs.vortex(x, y, eps=5.0, xc=5.0, yc=3.5, ly=7.0).astype(np.float32).astype(np.float64)
+    q_or, n_or, t_or = oracle.run(o, q0, 200)
+    with nat.Context(c) as ctx:
+        qd = to_dev(q0, c)
+        ctx.step(qd, 200)
+        q = host(qd)
+        t, steps = ctx.get_time()
+    assert steps == n_or == 200
+    assert t == pytest.approx(t_or, rel=1e-6)
+    assert rel_l2(q, q_or) <= TOL32
+
+
 @pytest.mark.parametrize("dtype", [nat.F64, nat.F32])
 def test_config2_fixed_steps(dtype):
     """Euler isentropic vortex, 128x128, p=3, periodic [0,10]^2, CFL steps: the
