@@ -256,6 +256,14 @@ const char* cpr_batch_last_error(const cpr_batch* b);
  * set of q_devs pointers between calls synchronises the stream once. */
 cpr_status cpr_batch_step(cpr_batch* b, void* const* q_devs, int nsteps, double dt_fixed, double t_end);
 
+/* Same as cpr_batch_step for states held in HOST memory: copies every
+ * q_in_host[i] (layout of cfgs[i]) to a batch-owned device array (allocated
+ * on first use), steps, copies the results to q_out_host[i] (may equal
+ * q_in_host[i]) and synchronises.  Pinned host memory gives the fastest
+ * copies. */
+cpr_status cpr_batch_step_host(cpr_batch* b, const void* const* q_in_host, void* const* q_out_host, int nsteps,
+                               double dt_fixed, double t_end);
+
 /* Autotuner: for each order group, times one RK3 step for each tile family
  * (8x8 and 16x4 elements per CTA) with one CTA per tile and with each
  * persistent grid of 1..max resident CTAs per SM smaller than that, and
@@ -292,22 +300,28 @@ cpr_status cpr_batch_set_time(cpr_batch* b, double t, long long steps);
  * owns the device memory (an allocation behind its back can fail or break
  * its accounting) or a latency-critical loop where cudaMalloc/cudaFree, which
  * may synchronise the device, are not allowed.
- *   cfg     problem description as for cpr_init; the limiter is not run
- *           (cfg->limiter != 0 returns CPR_EINVAL) and cfl is ignored.
+ *   cfg     problem description, validated as by cpr_init; in addition the
+ *           limiter must be off and the scheme CPR_SCHEME_CPR (CPR_EINVAL
+ *           otherwise); cfl is ignored.
  *   q_dev   device state array (layout and alignment as above), the only
  *           memory the caller provides; it holds the result.
  *   dt      step size (> 0); stream: cudaStream_t or NULL.
- * The two stage buffers and the control block live in one file-scope device
- * array of 2 * CPR_NOALLOC_MAX_STATE_BYTES + 256 bytes that every GPU loading
- * libcpr.so holds until the process exits.  A state larger than
- * CPR_NOALLOC_MAX_STATE_BYTES returns CPR_EINVAL before any work.  The first
- * call on each device looks up the array's device address
- * (cudaGetSymbolAddress) for that device; make that first call before any
- * stream capture.  All calls share the array and it keeps the previous
- * call's contents: each call rewrites the control block first, and calls
- * that overlap on the GPU (different streams, or host threads without
- * ordering between them) race on it.  Returns CPR_ECUDA if the symbol
- * lookup or a launch fails.  Simulated time is not tracked. */
+ * Arithmetic: the stages of cpr_step with a fixed step -- FP64 the
+ * Shu-Osher stages, FP32 the compensated increment form (the new state kept
+ * as a high and a low part, the low part cleared at the start of each call),
+ * so results equal those of cpr_step called with the same steps.
+ * The two stage buffers, the FP32 low part and the control block live in one
+ * file-scope device array of 3 * CPR_NOALLOC_MAX_STATE_BYTES + 256 bytes
+ * that every GPU loading libcpr.so holds until the process exits.  A state
+ * larger than CPR_NOALLOC_MAX_STATE_BYTES returns CPR_EINVAL before any
+ * work.  Every call looks up the array's device address on the current
+ * device (cudaGetSymbolAddress); the first call on a device also loads the
+ * kernels there, so make that first call before any stream capture.  All
+ * calls share the array and it keeps the previous call's contents: each call
+ * rewrites the control block and clears the low part first, and calls that
+ * overlap on the GPU (different streams, or host threads without ordering
+ * between them) race on it.  Returns CPR_ECUDA if the symbol lookup or a
+ * launch fails.  Simulated time is not tracked. */
 cpr_status cpr_step_noalloc(const cpr_config* cfg, void* q_dev, int nsteps, double dt, void* stream);
 
 #ifdef __cplusplus
