@@ -35,7 +35,8 @@ EXPORTS = (
     "cpr_residual", "cpr_step", "cpr_step_host", "cpr_limit", "cpr_get_marks", "cpr_averages",
     "cpr_norms", "cpr_set_time", "cpr_get_time", "cpr_residual_vjp", "cpr_step_vjp",
     "cpr_step_noalloc", "cpr_batch_init", "cpr_batch_destroy", "cpr_batch_last_error",
-    "cpr_batch_step", "cpr_batch_tune", "cpr_batch_set_form", "cpr_batch_get_time", "cpr_batch_set_time",
+    "cpr_batch_step", "cpr_batch_step_host", "cpr_batch_tune", "cpr_batch_set_form", "cpr_batch_get_time",
+    "cpr_batch_set_time",
 )
 
 
@@ -172,6 +173,8 @@ def load():
             lib.cpr_batch_last_error.argtypes = [P]
             lib.cpr_batch_step.restype = I
             lib.cpr_batch_step.argtypes = [P, ctypes.POINTER(P), I, D, D]
+            lib.cpr_batch_step_host.restype = I
+            lib.cpr_batch_step_host.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), I, D, D]
             lib.cpr_batch_tune.restype = I
             lib.cpr_batch_tune.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(I), ctypes.POINTER(I)]
             lib.cpr_batch_set_form.restype = I
@@ -373,6 +376,23 @@ class Batch:
         self._check(self.lib.cpr_batch_step(self.h, self._ptrs(qs), int(nsteps), float(dt_fixed),
                                             float(t_end)))
         return qs
+
+    def step_host(self, qs_in, qs_out=None, nsteps: int = 1, dt_fixed: float = 0.0, t_end: float = 0.0):
+        """cpr_batch_step on host (preferably pinned) tensors: copies in,
+        steps, copies out, synchronises."""
+        if qs_out is None:
+            qs_out = qs_in
+        if len(qs_in) != len(self.cfgs) or len(qs_out) != len(self.cfgs):
+            raise ValueError("one state per instance")
+        for group in (qs_in, qs_out):
+            for q, c in zip(group, self.cfgs):
+                if q.device.type != "cpu" or q.dtype != c.torch_dtype or not q.is_contiguous() \
+                        or q.numel() != c.nvars * c.ne * (c.p + 1) ** 2:
+                    raise ValueError("each state must be a contiguous host tensor of its instance's size")
+        pin = (ctypes.c_void_p * len(qs_in))(*[q.data_ptr() for q in qs_in])
+        pout = (ctypes.c_void_p * len(qs_out))(*[q.data_ptr() for q in qs_out])
+        self._check(self.lib.cpr_batch_step_host(self.h, pin, pout, int(nsteps), float(dt_fixed), float(t_end)))
+        return qs_out
 
     def tune(self, qs):
         choices = (ctypes.c_int * 12)()

@@ -57,6 +57,7 @@ struct cpr_batch {
     std::vector<LaunchCfg> lcs;
     std::vector<long long> nstate;
     std::vector<void*> Y, Z, lo;
+    std::vector<void*> host_state;  // device copies for cpr_batch_step_host (first use)
     Ctrl* ctrls = nullptr;
     Ctrl* h_ctrls = nullptr;      // pinned
     Ctrl* ctrl_backup = nullptr;  // device, for the autotuner
@@ -378,6 +379,7 @@ void free_batch(cpr_batch* b)
     for (void* p : b->Y) cudaFree(p);
     for (void* p : b->Z) cudaFree(p);
     for (void* p : b->lo) cudaFree(p);
+    for (void* p : b->host_state) cudaFree(p);
     for (Group& g : b->groups)
         for (int f = 0; f < cpr::kBatchFamilies; ++f) {
             cudaFree(g.d_inst[f]);
@@ -602,6 +604,44 @@ extern "C" cpr_status cpr_batch_step(cpr_batch* b, void* const* q, int nsteps, d
     } else {
         for (int k = 0; k < rest; ++k) BATCH_CUDA(b, cudaGraphLaunch(b->g1, b->stream));
     }
+    return CPR_OK;
+}
+
+extern "C" cpr_status cpr_batch_step_host(cpr_batch* b, const void* const* q_in, void* const* q_out, int nsteps,
+                                          double dt_fixed, double t_end)
+{
+    if (!b) return CPR_EINVAL;
+    if (!q_in || !q_out) {
+        b->err = "q_in_host and q_out_host must be non-NULL";
+        return CPR_EINVAL;
+    }
+    for (int i = 0; i < b->n; ++i)
+        if (!q_in[i] || !q_out[i]) {
+            b->err = "every host buffer must be non-NULL";
+            return CPR_EINVAL;
+        }
+    const size_t esize = b->dtype == CPR_F32 ? 4 : 8;
+    if (b->host_state.empty()) {
+        b->host_state.assign(b->n, nullptr);
+        for (int i = 0; i < b->n; ++i) {
+            const cudaError_t e = cudaMalloc(&b->host_state[i], (size_t)b->nstate[i] * esize);
+            if (e != cudaSuccess) {
+                for (void* p : b->host_state) cudaFree(p);
+                b->host_state.clear();
+                b->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+                return e == cudaErrorMemoryAllocation ? CPR_ENOMEM : CPR_ECUDA;
+            }
+        }
+    }
+    for (int i = 0; i < b->n; ++i)
+        BATCH_CUDA(b, cudaMemcpyAsync(b->host_state[i], q_in[i], (size_t)b->nstate[i] * esize,
+                                      cudaMemcpyHostToDevice, b->stream));
+    const cpr_status st = cpr_batch_step(b, b->host_state.data(), nsteps, dt_fixed, t_end);
+    if (st != CPR_OK) return st;
+    for (int i = 0; i < b->n; ++i)
+        BATCH_CUDA(b, cudaMemcpyAsync(q_out[i], b->host_state[i], (size_t)b->nstate[i] * esize,
+                                      cudaMemcpyDeviceToHost, b->stream));
+    BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
     return CPR_OK;
 }
 

@@ -157,4 +157,5 @@ def test_batch_init_rejects_unsupported_options(lib):
     h = ctypes.c_void_p()
     assert lib.cpr_batch_init(None, 1, None, ctypes.byref(h)) == _native.CPR_EINVAL
     assert lib.cpr_batch_step(None, None, 1, 0.0, 0.0) == _native.CPR_EINVAL
+    assert lib.cpr_batch_step_host(None, None, None, 1, 0.0, 0.0) == _native.CPR_EINVAL
     lib.cpr_batch_destroy(None)

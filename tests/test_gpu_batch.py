@@ -144,3 +144,22 @@ def test_batch_tune_keeps_states_and_results():
     ref, _ = singles(cs, q0s, 4, 0.004)
     for q, r in zip(qs, ref):
         assert rel(q, r) <= TOL[nat.F32]
+
+
+def test_batch_step_host_matches_device_step():
+    """cpr_batch_step_host (host buffers, copies inside the call) gives the
+    states of cpr_batch_step on device arrays, on two calls in a row."""
+    cs = cfgs(nat.F32)
+    q0s = [initial(c, s[3]) for c, s in zip(cs, SHAPES)]
+    with nat.Batch(cs) as b:
+        qd = [q.clone() for q in q0s]
+        b.step(qd, 3, 0.004)
+        b.step(qd, 2, 0.004)
+    with nat.Batch(cs) as b:
+        hin = [q.cpu().pin_memory() for q in q0s]
+        hout = [torch.empty_like(h).pin_memory() for h in hin]
+        b.step_host(hin, hout, 3, 0.004)
+        b.step_host(hout, hout, 2, 0.004)
+        assert all(b.get_time(i)[1] == 5 for i in range(len(cs)))
+    for d, h in zip(qd, hout):
+        assert torch.equal(d.cpu(), h)
