@@ -389,7 +389,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
     const bool valid = active && tx < TXe && ty < TYe;
     const long long e = (long long)(j0 + ty) * A.nx + (i0 + tx);
     const bool addb = A.mode == MODE_INC2 || A.mode == MODE_INC3;
-    const bool lwall = A.bcx && i0 + tx == 0, bwall = A.bcy && j0 + ty == 0;
+    const bool lwall = A.bcx && i0 + tx == 0;
 
     // ---- phase 1: own row -> tile copy and x-line; halo lines --------------
     T rx[N][V];           // d/dxi of the flux differences along row k
@@ -562,16 +562,27 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
     }
     __syncthreads();
 
-    // ---- phase 2: y-line (column k of the element) ---------------------------
-    T ry[N][V];           // d/deta of the flux differences along column k
+    // ---- phase 2: y-line (column kc of element elc) --------------------------
+    // Column identity of the thread.  Odd N: k-major (a warp holds one column
+    // of 32 consecutive elements), so that the column accesses of the tile
+    // copy (odd element stride) and of the y-derivatives meet no bank
+    // conflict; the element-major identity would put two elements' columns
+    // in one bank.  Even N: the row identity (the N = 4 swizzle makes both
+    // access patterns conflict-free for it).
+    constexpr bool KMAJ = (N % 2 == 1) && !DELTA;
+    const int elc = KMAJ ? tid % (TX * TY) : el, kc = KMAJ ? tid / (TX * TY) : k;
+    const int txc = elc % TX, tyc = elc / TX;
+    const bool validc = active && txc < TXe && tyc < TYe;
+    const bool bwallc = A.bcy && j0 + tyc == 0;
+    T ry[N][V];           // d/deta of the flux differences along column kc
     T eB[V], gB[V];       // own bottom edge state and flux
-    if (valid) {
+    if (validc) {
         T d[N][V], g[N][V], col[N], eT[V], gT[V];
 #pragma unroll
         for (int b = 0; b < N; ++b)
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                const T x = sq[L::sq(v, el, b, k)];
+                const T x = sq[L::sq(v, elc, b, kc)];
                 d[b][v] = DELTA ? x - rf.q[v] : x;
             }
         if constexpr (PAIRED) {
@@ -622,14 +633,14 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
         }
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            yT[L::yt(v, ty + 1, tx, k)] = eT[v];
-            yF[L::ef(v, el, k)] = gT[v];
+            yT[L::yt(v, tyc + 1, txc, kc)] = eT[v];
+            yF[L::ef(v, elc, kc)] = gT[v];
         }
         if constexpr (L::RYSEP) {
 #pragma unroll
             for (int b = 0; b < N; ++b)
 #pragma unroll
-                for (int v = 0; v < V; ++v) ryS[L::sq(v, el, b, k)] = ry[b][v];
+                for (int v = 0; v < V; ++v) ryS[L::sq(v, elc, b, kc)] = ry[b][v];
         }
     }
     __syncthreads();
@@ -642,13 +653,34 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
     // neighbour's (over the neighbour's edge flux in shared memory, shifted to
     // the neighbour's reference).
     T JL[V];
-    if (valid) {
-        if constexpr (!L::RYSEP) {
+    if (validc && !L::RYSEP) {
 #pragma unroll
-            for (int b = 0; b < N; ++b)
+        for (int b = 0; b < N; ++b)
 #pragma unroll
-                for (int v = 0; v < V; ++v) ryS[L::sq(v, el, b, k)] = ry[b][v];
+            for (int v = 0; v < V; ++v) ryS[L::sq(v, elc, b, kc)] = ry[b][v];
+    }
+    // lower face of column kc of element elc (column identity); in the delta
+    // form (row identity = column identity) relative to the element's
+    // reference rf0 with state q0
+    auto lower_face = [&](const Ref<T>& rf0, const T (&q0)[V]) {
+        T o[V], dm[V], G[V], sh[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) o[v] = (DELTA && !bwallc) ? rfS[L::rf(v, txc, tyc - 1)] - q0[v] : T(0);
+#pragma unroll
+        for (int v = 0; v < V; ++v) dm[v] = bwallc ? eB[v] : yT[L::yt(v, tyc, txc, kc)] + o[v];
+        face_flux<EQ, FLUX, 1, DELTA>(rf0, dm, eB, A.ph, G);
+#pragma unroll
+        for (int v = 0; v < V; ++v) jB[L::ef(v, elc, kc)] = G[v] - gB[v];
+        if (tyc > 0) {
+            if constexpr (DELTA) dflux<EQ, 1>(rf0, o, A.ph, sh);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                T* pj = yF + L::ef(v, elc - TX, kc);
+                *pj = (DELTA ? G[v] - sh[v] : G[v]) - *pj;
+            }
         }
+    };
+    if (valid) {
         T q0[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) q0[v] = DELTA ? rfS[L::rf(v, tx, ty)] : T(0);
@@ -671,21 +703,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
                 *pj = (DELTA ? G[v] - sh[v] : G[v]) - *pj;
             }
         }
-        // lower face
-#pragma unroll
-        for (int v = 0; v < V; ++v) o[v] = (DELTA && !bwall) ? rfS[L::rf(v, tx, ty - 1)] - q0[v] : T(0);
-#pragma unroll
-        for (int v = 0; v < V; ++v) dm[v] = bwall ? eB[v] : yT[L::yt(v, ty, tx, k)] + o[v];
-        face_flux<EQ, FLUX, 1, DELTA>(rf, dm, eB, A.ph, G);
-#pragma unroll
-        for (int v = 0; v < V; ++v) jB[L::ef(v, el, k)] = G[v] - gB[v];
-        if (ty > 0) {
-            if constexpr (DELTA) dflux<EQ, 1>(rf, o, A.ph, sh);
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                T* pj = yF + L::ef(v, el - TX, k);
-                *pj = (DELTA ? G[v] - sh[v] : G[v]) - *pj;
-            }
+        if constexpr (!KMAJ) lower_face(rf, q0);
+    }
+    if constexpr (KMAJ) {
+        if (validc) {
+            const T q0[V] = {};
+            lower_face(rf, q0);
         }
     }
     if (tid < (TX + TY) * N) {
