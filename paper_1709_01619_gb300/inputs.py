@@ -107,6 +107,15 @@ def perturbed(q: np.ndarray, seed: int, rel: float = 1e-2) -> np.ndarray:
     return q * (1.0 + noise(q.shape, seed, rel))
 
 
+# CFL number per order for the batch of vortices (Eq. 36 takes the speed
+# |V| + c).  The linear stability bound of three-stage SSP Runge-Kutta with
+# this scheme in 1D is about 0.21, 0.13 and 0.09 for p = 2, 3, 4 (|a| dt / h);
+# in 2D the step must also cover (|u| + c) / hx + (|v| + c) / hy, which for a
+# flow along the diagonal of a weak vortex is about 0.6 times the 1D bound in
+# these units.  These values keep a margin of about 25-30 % below that.
+BATCH_CFL = {2: 0.1, 3: 0.06, 4: 0.04}
+
+
 def batch_instances(count: int = 64, seed: int = 0):
     """Ragged batch of vortex solves: per instance N ~ U{32..256} elements per
     side, p ~ U{2,3,4}, strength eps ~ U[1,5], all drawn from one seed."""

@@ -18,7 +18,7 @@ def cfgs(dtype):
     out = []
     for i, (nx, ny, p, _) in enumerate(SHAPES):
         h = 0.4 + 0.1 * i  # element size differs between instances
-        cfl = {1: 0.2, 2: 0.1, 3: 0.08, 4: 0.06}[p]  # stable SSP-RK3 CFL per order
+        cfl = {1: 0.2, **inputs.BATCH_CFL}[p]  # stable SSP-RK3 CFL per order
         out.append(nat.Config(eqn=nat.EULER, nx=nx, ny=ny, p=p, x1=nx * h, y1=ny * h, cfl=cfl,
                               dtype=dtype))
     return out
