@@ -132,19 +132,26 @@ __device__ __forceinline__ void load_elements_all(const T* __restrict__ q, long 
     }
 }
 
-// One edge point of the marking test, without branches.  d: the outward
-// edge deviation; c: the minmod of the two neighbour-average differences
-// across the edge (zero unless they share a sign); mh2 = M h^2.  The point is
-// troubled when |d| > M h^2 and |d - minmod(d, D+, D-)| > eps, where the
+// Bounds of the marking test along one direction.  With A = M h^2, c the
+// minmod of the two neighbour-average differences across the edge (zero
+// unless they share a sign) and the outward edge deviation d, a point is
+// troubled when |d| > A and |d - minmod(d, D+, D-)| > eps, where the
 // three-argument minmod is min(d, c) for d, c > 0, max(d, c) for d, c < 0,
-// else 0: the same values, and so the same decision, as the TVB minmod
-// written out.
+// else 0 (the TVB minmod keeps d itself when |d| <= A, where the point is
+// not troubled either way).  On each side of zero that test is monotone in
+// d, so it is the same as d > hi or d < lo with
+//   c > 0:  hi = max(A, c + eps),  lo = -max(A, eps)
+//   c < 0:  hi = max(A, eps),      lo = min(-A, c - eps)
+//   c = 0:  hi = max(A, eps),      lo = -max(A, eps)
+// and an edge is troubled exactly when its largest deviation exceeds hi or
+// its smallest is below lo: two comparisons per edge instead of a minmod
+// test per edge point.
 template <class T>
-__device__ __forceinline__ bool tvb_troubled(T d, T c, T mh2, T eps)
+__device__ __forceinline__ void tvb_bounds(T c, T mh2, T eps, T& lo, T& hi)
 {
-    const T mm = d > T(0) ? (c > T(0) ? ::fmin(d, c) : T(0)) : (c < T(0) ? ::fmax(d, c) : T(0));
-    const T r = d - mm;
-    return (d >= T(0) ? d : -d) > mh2 && (r >= T(0) ? r : -r) > eps;
+    const T a = ::fmax(mh2, eps);
+    hi = c > T(0) ? ::fmax(mh2, c + eps) : a;
+    lo = c < T(0) ? ::fmin(-mh2, c - eps) : -a;
 }
 
 // Troubled-cell limiter.  One thread per (element, variable), variable-major
@@ -155,7 +162,8 @@ __device__ __forceinline__ bool tvb_troubled(T d, T c, T mh2, T eps)
 // -1 on left/bottom) is compared with the TVB minmod of delta and the
 // differences of the neighbouring averages across that edge; the element is
 // marked when |delta - mt| > eps anywhere (the OR over edge points and
-// variables of Algorithm 11, taken in shared memory).  Limiting (Eq. 35, per
+// variables of Algorithm 11, taken in shared memory), tested through the
+// extreme deviations of each edge against the bounds of tvb_bounds.  Limiting (Eq. 35, per
 // direction): q_ab = qbar + (xi_a hx / 2) mm(Dx+ / hx, Dx- / hx)
 // + (eta_b hy / 2) mm(Dy+ / hy, Dy- / hy).  A transmissive boundary
 // contributes a ghost average equal to the element's own average.  The fused
@@ -211,10 +219,15 @@ __global__ void __launch_bounds__(LimShape<T, P, EQ>::NT) cpr_limit_kernel(const
 #pragma unroll
         for (int pt = 0; pt < NN; ++pt) vals[pt] = mine[pt];
         // minmod of the neighbour differences per direction (zero unless
-        // both share a sign), and M h^2 per direction
+        // both share a sign), M h^2 per direction, and the bounds of the
+        // outward deviation (tvb_bounds)
         const T cx = minmod2(aR - qk, qk - aL), cy = minmod2(aT - qk, qk - aB);
-        const T mh2x = A.tvb_M * A.hx * A.hx, mh2y = A.tvb_M * A.hy * A.hy;
-        bool troubled = false;
+        T lox, hix, loy, hiy;
+        tvb_bounds(cx, A.tvb_M * A.hx * A.hx, A.lim_eps, lox, hix);
+        tvb_bounds(cy, A.tvb_M * A.hy * A.hy, A.lim_eps, loy, hiy);
+        // extreme edge values per edge: the outward deviation is q_edge - qbar
+        // on the right / top edges and qbar - q_edge on the left / bottom ones
+        T mnL = T(0), mxL = T(0), mnR = T(0), mxR = T(0), mnB = T(0), mxB = T(0), mnT = T(0), mxT = T(0);
 #pragma unroll
         for (int kk = 0; kk < N; ++kk) {
             T row[N], col[N];
@@ -232,11 +245,17 @@ __global__ void __launch_bounds__(LimShape<T, P, EQ>::NT) cpr_limit_kernel(const
                 sB = fma(tb.lm[l], col[l], sB);
                 sT = fma(tb.lp[l], col[l], sT);
             }
-            troubled |= tvb_troubled(qk - sL, cx, mh2x, A.lim_eps);
-            troubled |= tvb_troubled(sR - qk, cx, mh2x, A.lim_eps);
-            troubled |= tvb_troubled(qk - sB, cy, mh2y, A.lim_eps);
-            troubled |= tvb_troubled(sT - qk, cy, mh2y, A.lim_eps);
+            mnL = kk ? ::fmin(mnL, sL) : sL;
+            mxL = kk ? ::fmax(mxL, sL) : sL;
+            mnR = kk ? ::fmin(mnR, sR) : sR;
+            mxR = kk ? ::fmax(mxR, sR) : sR;
+            mnB = kk ? ::fmin(mnB, sB) : sB;
+            mxB = kk ? ::fmax(mxB, sB) : sB;
+            mnT = kk ? ::fmin(mnT, sT) : sT;
+            mxT = kk ? ::fmax(mxT, sT) : sT;
         }
+        const bool troubled = (qk - mnL > hix) | (qk - mxL < lox) | (mxR - qk > hix) | (mnR - qk < lox) |
+                              (qk - mnB > hiy) | (qk - mxB < loy) | (mxT - qk > hiy) | (mnT - qk < loy);
         if (troubled) s_mark[le] = 1;  // every writer stores 1
     }
     __syncthreads();
