@@ -1,24 +1,35 @@
 #!/usr/bin/env python
 """CPR benchmark: DOF-stage updates/s of the SSP-RK3 CPR solver on GB300.
 
-Workload (one bench "step" = one whole solve): the 2D Euler isentropic vortex
-(gamma 1.4, strength 5, centred at (5, 5), mean flow (1, 1)) on the periodic
-box [0,10]^2 with 128 x 128 elements, CPR p = 3 (16 Gauss points per element,
-4 conserved variables), Rusanov flux, g_DG correction, SSP-RK3 with device-side
-CFL steps (CFL 0.08) to t = 10.  The headline value is the FP32 path; the FP64
-path runs the same solve once and both report their L2 error of the density
-averages against the exact solution (which at t = 10 equals the initial field).
+Headline workload (one bench "step" = one pass of the whole hot path over
+one batch of synthetic input): 64 isentropic-vortex problems of the 2D Euler
+equations (gamma 1.4, mean flow (1, 1), centred at (5, 5) on the periodic box
+[0,10]^2; per instance N x N elements with N ~ U{32..256}, CPR order
+p ~ U{2,3,4}, vortex strength ~ U[1,5], all drawn from numpy seed 0), Gauss
+points, Rusanov flux, g_DG correction, advanced together by the batched
+solver for 100 SSP-RK3 steps with per-instance device-side CFL steps
+(CFL 0.1 / 0.06 / 0.04 for p = 2 / 3 / 4, below the stability bound), FP32 state with the compensated
+increment form, FP64 time and reductions.  The autotuner picks the batch
+form before the timed region.  Each timed pass starts from the same initial
+states (reset outside the timed events); the states (445 MB per array) are
+larger than L2.
 
-    value = 128 * 128 * 16 * 3 * (RK3 steps) * K / (sum of the K solve times)
+    value = sum_i N_i^2 (p_i+1)^2 * 3 * 100 * K / (sum of the K pass times)
 
-summed over ranks (each rank solves its own replica; no data-path collective).
-L2 is flushed (a 256 MiB write) before every timed solve, outside its events.
-The roofline object covers the dominant kernel (the fused residual + RK stage
-kernel): algorithmic bytes per launch (8 state arrays per RK3 step: 8/3 * 4
-variables * 4 B = 42.7 B per point and stage) over its mean launch duration;
-the FP32 compensated increment form actually moves 10 arrays per step (53.3 B),
-reported as moved_gbs.  A second roofline block repeats this on a 1024 x 1024
-vortex whose state (268 MB per array) is larger than L2.
+summed over ranks (each rank advances its own replica of the batch; no
+data-path collective).  The roofline object covers the stage kernels, the
+dominant kernels of the pass: algorithmic bytes of one batch stage (8 state
+arrays per RK3 step: 8/3 * 4 variables * 4 B = 42.7 B per DOF) over the mean
+time of one batch stage; the compensated FP32 form moves 10 arrays per step.
+`e2e` is the same pass through cpr_batch_step_host with pinned host buffers
+(every state copied in and the results copied out inside the timed region).
+
+Beside it (compact keys, full records on stderr): the single-problem stage
+kernel on the 1024^2 p = 3 vortex (268 MB per array), the 128^2 p = 3 vortex
+to t = 10 in FP32 and FP64 with both density-average errors, the time to a
+given error of FP32 and FP64 over a ladder of grids, the limited four-quadrant
+run, the FV equal-DOF runs, the radial shock tube, the adjoint, the paper's
+point set and divergence, and the oracle on the host cores.
 """
 from __future__ import annotations
 
@@ -26,6 +37,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -39,6 +51,8 @@ if ROOT not in sys.path:
 
 METRIC = "CPR DOF-stage updates/s (FP32 vs FP64, equal L2 error) and % HBM roofline"
 UNIT = "DOF-stage/s"
+WORKLOAD = "batch_64_euler_vortex_N32-256_p2-4_fp32_100_rk3_steps"
+BATCH_N, BATCH_SEED, BATCH_STEPS = 64, 0, 100
 NX, P, L, EPS, T_END, CFL = 128, 3, 10.0, 5.0, 10.0, 0.08
 HBM_NX, HBM_STEPS = 1024, 20
 # Algorithmic bytes of one DOF-stage (one solution point, all 4 variables):
@@ -51,26 +65,34 @@ HBM_NX, HBM_STEPS = 1024, 20
 ALGO_ARRAYS_PER_STEP = 8
 MOVED_ARRAYS_PER_STEP = 10
 # DRAM bytes (read + write) per stage launch, mean over the three RK stages,
-# from ncu captures of the stage kernel as it stands (profiles/): the
-# 128^2 workload replayed cold (writes stay in L2) and the 1024^2 case.
+# from ncu captures of the stage kernel (profiles/): the 128^2 workload
+# replayed cold (writes stay in L2) and the 1024^2 case.
 NCU_TRAFFIC_128 = 8.429e6
 NCU_TRAFFIC_1024 = 8.573e8
 FALLBACK_HBM_GBS = 6800.0
-# FP64 floating-point operations per DOF-stage of the 128^2 p = 3 Euler stage
-# kernel (2 per DFMA, 1 per DMUL / DADD, counted by ncu over the three RK
-# stages; IEEE division and square root are DFMA sequences), and the FP64
-# peak derived from GB300's units: 152 SMs x 2 FP64 FMA per SM per clock x 2
-# flops x 2.07 GHz = 1.26 TFLOP/s (the nominal 1.25).
-FP64_FLOPS_PER_DOF_STAGE = 297.4
+# FP64 floating-point operations per DOF-stage of the Euler LP stage at
+# p = 3: the method's own count (point fluxes about 25, the two line
+# derivatives 4 V n 2 = 128, the correction 4 V 2 = 32 and the face fluxes
+# about 60 per face point, 60 * 4n / n^2 = 15; about 200), and the count the
+# FP64 stage kernel executes (2 per DFMA, 1 per DMUL / DADD, counted by ncu
+# over the three RK stages of the 128^2 p = 3 vortex: 297.4, with index
+# arithmetic in FP64 and IEEE division and square root as DFMA sequences).
+# The FP64 peak is derived from GB300's units, not measured: 152 SMs x 2 FP64
+# FMA per SM per clock x 2 flops x 2.07 GHz = 1.26 TFLOP/s (the nominal 1.25).
+FP64_FLOPS_ALGO = 200.0
+FP64_FLOPS_EXECUTED = 297.4
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Coarser grids of the equal-error ladder (p = 3 vortex to t = 10, beside 128^2).
+LADDER = (24, 32, 48, 64, 96)
 
 
 def f64_roofline(rate):
-    if FP64_FLOPS_PER_DOF_STAGE is None:
-        return {"bound": "alu", "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "achieved": None, "frac": None}
-    a = rate * FP64_FLOPS_PER_DOF_STAGE / 1e12
+    a = rate * FP64_FLOPS_ALGO / 1e12
     return {"bound": "alu", "achieved": a, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": a / FP64_PEAK_TFLOPS, "flops_per_dof_stage": FP64_FLOPS_PER_DOF_STAGE}
+            "frac": a / FP64_PEAK_TFLOPS, "flops_per_dof_stage": FP64_FLOPS_ALGO,
+            "executed_flops_per_dof_stage": FP64_FLOPS_EXECUTED,
+            "executed_frac": rate * FP64_FLOPS_EXECUTED / 1e12 / FP64_PEAK_TFLOPS,
+            "peak_source": "derived from unit counts and clock, not measured"}
 
 
 def parse():
@@ -80,14 +102,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cpr", "reference"], default="cpr")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["vortex128", "vortex1024", "batch", "fv1536", "limited", "radial", "f64"],
-                    default="vortex128", help="vortex1024 / batch / fv1536 / limited / radial / f64: "
-                    "only that block (short runs for profiling)")
+    ap.add_argument("--workload", choices=["headline", "vortex128", "vortex1024", "batch", "fv1536", "limited",
+                                           "radial", "f64", "ladder", "adjoint"],
+                    default="headline", help="anything but headline: only that block (short runs for "
+                    "profiling)")
+    ap.add_argument("--p", type=int, default=P, help="--workload vortex1024: the order")
     ap.add_argument("--no-tune", action="store_true",
                     help="--workload batch: the untuned launch (for profilers, whose serialised replays "
                     "distort the autotuner's timings)")
-    ap.add_argument("--quick", action="store_true",
-                    help="FP32 timed solves only (no FP64 solve, e2e, HBM case or CPU baseline)")
+    ap.add_argument("--quick", action="store_true", help="the headline only (no side blocks, no CPU baseline)")
     return ap.parse_args()
 
 
@@ -98,6 +121,38 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+def compact(x, sig=4):
+    """Floats rounded to `sig` significant digits, recursively (the printed line)."""
+    if isinstance(x, float):
+        if x == 0.0 or not math.isfinite(x):
+            return x
+        return float(f"{x:.{sig}g}")
+    if isinstance(x, dict):
+        return {k: compact(v, sig) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [compact(v, sig) for v in x]
+    return x
+
+
+def cpu_model():
+    """The host CPU's model name (x86 /proc/cpuinfo, else lscpu, else platform)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
 
 
 def exact_rho_averages(nx):
@@ -203,68 +258,191 @@ def sum_over_ranks(x, world):
 
 
 # ---------------------------------------------------------------------------
+# the headline workload: 64 ragged vortex instances
+# ---------------------------------------------------------------------------
+def batch_specs():
+    from paper_1709_01619_gb300 import inputs
+    return inputs.batch_instances(BATCH_N, seed=BATCH_SEED)
+
+
+def batch_dof(specs=None):
+    specs = specs or batch_specs()
+    return sum(s["N"] * s["N"] * (s["p"] + 1) ** 2 for s in specs)
+
+
+# ---------------------------------------------------------------------------
 # oracle on the host cores (CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample(target_s=12.0):
-    """Time the FP64 oracle on the 128^2 p=3 vortex for a bounded number of
-    SSP-RK3 steps (about target_s seconds).  Returns (DOF-stage/s, steps, s,
-    threads)."""
+def oracle_batch_states(every=1):
+    """Oracle configurations and FP64 initial states of every `every`-th
+    instance of the headline batch."""
     import oracle
     from paper_1709_01619_gb300 import inputs
-    o = oracle.Config(eqn=oracle.EULER, nx=NX, ny=NX, p=P, x1=L, y1=L, cfl=CFL)
-    x, y = oracle.point_coords(o)
-    q = inputs.vortex(x, y, eps=EPS)
-    t0 = time.perf_counter()
-    q, _, _ = oracle.run(o, q, 1)
-    t1 = time.perf_counter() - t0
-    steps = int(max(1, min(400, target_s / max(t1, 1e-6))))
-    t0 = time.perf_counter()
-    oracle.run(o, q, steps)
-    dt = time.perf_counter() - t0
-    dof = NX * NX * (P + 1) ** 2
-    return dof * 3 * steps / dt, steps, dt, oracle.threads()
+    out = []
+    for s in batch_specs()[::every]:
+        o = oracle.Config(eqn=oracle.EULER, nx=s["N"], ny=s["N"], p=s["p"], x1=L, y1=L, cfl=inputs.BATCH_CFL[s["p"]])
+        x, y = oracle.point_coords(o)
+        out.append((o, inputs.vortex(x, y, eps=s["eps"])))
+    return out
+
+
+def oracle_batch_sample(steps=1, every=1, threads=None, states=None):
+    """Time the FP64 oracle on `steps` CFL RK3 steps of every `every`-th
+    instance of the headline batch (the initial states built outside the
+    timing).  threads: OpenMP threads for the sample (None: all).
+    Returns (DOF-stage/s, DOF-stages, s, threads used)."""
+    import oracle
+    states = states if states is not None else oracle_batch_states(every)
+    prev = oracle.threads()
+    if threads:
+        oracle.set_threads(threads)
+    try:
+        used = oracle.threads()
+        work = 0
+        t0 = time.perf_counter()
+        for o, q in states:
+            oracle.run(o, q, steps)
+            work += o.ne * o.n * o.n * 3 * steps
+        secs = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(prev)
+    return work / secs, work, secs, used
 
 
 def run_reference(args, world, rank):
+    """The reference arm: the FP64 oracle (the plain CPU restatement of the
+    method that the tests check the CUDA path against) on the host cores,
+    each step one CFL RK3 step of all 64 instances of the headline batch."""
     if rank != 0:
         return
-    per_step_target = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    states = oracle_batch_states()
     for _ in range(args.warmup):
-        oracle_sample(per_step_target)
-    vals, secs, nsteps = [], 0.0, 0
-    threads = 1
+        oracle_batch_sample(1, states=states)
+    work, secs, threads = 0, 0.0, 1
     for _ in range(args.steps):
-        v, s, dt, threads = oracle_sample(per_step_target)
-        vals.append(v)
-        secs += dt
-        nsteps += s
-    dof = NX * NX * (P + 1) ** 2
-    value = dof * 3 * nsteps / secs
-    sample = (f"{nsteps} SSP-RK3 steps of the 128x128 p=3 vortex in FP64 over {args.steps} samples "
-              f"(the full solve to t=10 is about 5400 steps)")
+        _, w, s, threads = oracle_batch_sample(1, states=states)
+        work += w
+        secs += s
+    value = work / secs
+    sample = (f"1 FP64 SSP-RK3 CFL step of all 64 instances per bench step, {args.steps} steps "
+              f"(the GPU arm advances each pass by {BATCH_STEPS} steps)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "euler_vortex_128x128_p3_t10", "nx": NX, "ny": NX, "p": P,
-                   "t_end": T_END, "cfl": CFL, "precision": "fp64", "l2_flush": "n/a (host)"},
+        "config": {"workload": WORKLOAD, "instances": BATCH_N, "seed": BATCH_SEED, "dof": batch_dof(),
+                   "precision": "fp64", "l2_flush": "n/a (host)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "cpu": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    print(json.dumps(compact(line)), flush=True)
 
 
 # ---------------------------------------------------------------------------
 # CUDA path
 # ---------------------------------------------------------------------------
-def hbm_case(make, peak, steps=HBM_STEPS):
-    """1024^2 p=3 FP32 vortex (268 MB per state array, above L2): the stage
-    kernels of `steps` RK3 steps timed back to back with CUDA events."""
+def batch_inputs(specs=None):
+    """Configurations and FP32 device initial states of the headline batch."""
     import torch
     from paper_1709_01619_gb300 import _native as nat
-    cfgH, ctxH, q0H = make(nat.F32, HBM_NX)
+    from paper_1709_01619_gb300 import inputs
+    specs = specs or batch_specs()
+    cfgs = [nat.Config(eqn=nat.EULER, nx=s["N"], ny=s["N"], p=s["p"], x1=L, y1=L, dtype=nat.F32,
+                       cfl=inputs.BATCH_CFL[s["p"]]) for s in specs]
+    q0s = []
+    for c, s in zip(cfgs, specs):
+        with nat.Context(c) as ctx:
+            x, y = ctx.point_coords()
+        q0s.append(torch.tensor(inputs.vortex(x, y, eps=s["eps"]), dtype=torch.float32, device="cuda"))
+    return cfgs, q0s
+
+
+def batch_headline(args, world, local, peak):
+    """The headline: K timed passes of the batch (BATCH_STEPS CFL steps each)
+    after autotuning and W untimed passes; then the same passes through the
+    host-buffer entry point for e2e."""
+    import torch
+    from paper_1709_01619_gb300 import _native as nat
+    cfgs, q0s = batch_inputs()
+    dof = batch_dof()
+    qs = [q.clone() for q in q0s]
+    out = {}
+    with nat.Batch(cfgs) as b:
+        choices = b.tune(qs)
+        per_inst = bool(choices) and choices[0][1] == 2
+        ngroups = len(choices)
+
+        def reset():
+            for q, q0 in zip(qs, q0s):
+                q.copy_(q0)
+            b.set_time(0.0, 0)
+
+        for _ in range(args.warmup):
+            reset()
+            b.step(qs, BATCH_STEPS)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        clocks = ClockSampler(local)
+        barrier(world)
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            reset()
+            evs[k][0].record()
+            b.step(qs, BATCH_STEPS)
+            evs[k][1].record()
+        torch.cuda.synchronize()
+        barrier(world)
+        clk = clocks.stop()
+        ms = sum(a.elapsed_time(e) for a, e in evs)
+        steps_done = [b.get_time(i)[1] for i in range(len(cfgs))]
+        t_reached = [b.get_time(i)[0] for i in range(len(cfgs))]
+        finite = all(bool(torch.isfinite(q).all()) for q in qs)
+
+        # e2e: the same pass through cpr_batch_step_host, pinned host buffers
+        hin = [q.cpu().pin_memory() for q in q0s]
+        hout = [torch.empty_like(h).pin_memory() for h in hin]
+        b.set_time(0.0, 0)
+        b.step_host(hin, hout, BATCH_STEPS)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            b.set_time(0.0, 0)
+            b.step_host(hin, hout, BATCH_STEPS)
+        e2e_s = time.perf_counter() - t0
+        e2e_equal = all(torch.equal(h, q.cpu()) for h, q in zip(hout, qs))
+    ms_max = max_over_ranks(ms, world)
+    updates = dof * 3 * BATCH_STEPS * args.steps
+    value = sum_over_ranks(updates, world) / (ms_max * 1e-3)
+    e2e = sum_over_ranks(updates, world) / max_over_ranks(e2e_s, world)
+    stage_ms = ms / (args.steps * 3 * BATCH_STEPS)
+    bytes_per_stage = dof * 16 * ALGO_ARRAYS_PER_STEP / 3.0
+    achieved = bytes_per_stage / (stage_ms * 1e-3) / 1e9
+    state_bytes = dof * 16
+    kernels_per_step = 3 * (len(cfgs) if per_inst else ngroups)
+    out.update(
+        value=value, ms=ms, ms_max=ms_max, dof=dof, clocks=clk, finite=finite, steps_done=steps_done,
+        t_min=min(t_reached), t_max=max(t_reached), e2e=e2e, e2e_equal=e2e_equal, state_bytes=state_bytes,
+        tuned=[{"p": p, "family": f, "grid": g} for p, f, g in choices], per_instance=per_inst,
+        roofline={"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                  "traffic": None, "unit_of_work": "one batch stage (all 64 instances)",
+                  "bytes_per_stage": bytes_per_stage, "stage_ms": stage_ms,
+                  "moved_frac": achieved * MOVED_ARRAYS_PER_STEP / ALGO_ARRAYS_PER_STEP / peak,
+                  "kernel": "cpr_stage_kernel<float,p,Euler,LP,Rusanov> (p = 2, 3, 4)"},
+        # per pass: the stage kernels, the configure kernel, one first-CFL
+        # pass per instance and one parity-copy kernel per order group
+        gpu_launches=args.steps * (BATCH_STEPS * kernels_per_step + 1 + len(cfgs) + ngroups))
+    return out
+
+
+def hbm_case(make, peak, steps=HBM_STEPS, p=P):
+    """1024^2 FP32 vortex of order p (p = 3: 268 MB per state array, above
+    L2): the stage kernels of `steps` RK3 steps timed back to back with CUDA
+    events."""
+    import torch
+    from paper_1709_01619_gb300 import _native as nat
+    cfgH, ctxH, q0H = make(nat.F32, HBM_NX, p)
     qH = q0H.clone()
     ctxH.step(qH, 3, 1e-4)
     torch.cuda.synchronize()
@@ -274,15 +452,142 @@ def hbm_case(make, peak, steps=HBM_STEPS):
     eh[1].record()
     torch.cuda.synchronize()
     msH = eh[0].elapsed_time(eh[1])
-    dofH = HBM_NX * HBM_NX * (P + 1) ** 2
+    dofH = HBM_NX * HBM_NX * (p + 1) ** 2
     launchH = msH / (3 * steps)
     achievedH = dofH * 16 * ALGO_ARRAYS_PER_STEP / 3.0 / (launchH * 1e-3) / 1e9
     movedH = achievedH * MOVED_ARRAYS_PER_STEP / ALGO_ARRAYS_PER_STEP
     ctxH.close()
-    return {"workload": "euler_vortex_1024x1024_p3_fp32", "bound": "hbm", "achieved": achievedH,
-            "peak": peak, "unit": "GB/s", "frac": achievedH / peak, "traffic": NCU_TRAFFIC_1024,
+    return {"workload": f"euler_vortex_{HBM_NX}x{HBM_NX}_p{p}_fp32", "bound": "hbm", "achieved": achievedH,
+            "peak": peak, "unit": "GB/s", "frac": achievedH / peak,
+            "traffic": NCU_TRAFFIC_1024 if p == 3 else None,
             "moved_gbs": movedH, "moved_frac": movedH / peak, "launch_ms": launchH,
             "dof_stage_per_s": dofH * 3 * steps / (msH * 1e-3), "rk3_steps": steps}
+
+
+def make_vortex(dtype, nx=NX, p=P):
+    import torch
+    from paper_1709_01619_gb300 import _native as nat
+    from paper_1709_01619_gb300 import inputs
+    cfg = nat.Config(eqn=nat.EULER, nx=nx, ny=nx, p=p, x1=L, y1=L, cfl=CFL, dtype=dtype)
+    ctx = nat.Context(cfg)
+    x, y = ctx.point_coords()
+    q0 = torch.tensor(inputs.vortex(x, y, eps=EPS), dtype=cfg.torch_dtype, device="cuda")
+    return cfg, ctx, q0
+
+
+def vortex_solve(dtype, nx, p=P, repeats=1, flush=None):
+    """The vortex on nx^2 elements of order p solved to t = 10 (CFL steps on
+    the device): the step count from an untimed solve, then `repeats` timed
+    solves from the initial state (L2 flushed before each when given).
+    Returns (mean ms, RK3 steps, density-average error, final state)."""
+    import torch
+    cfg, ctx, q0 = make_vortex(dtype, nx, p)
+    with ctx:
+        q = q0.clone()
+        ctx.set_time(0.0, 0)
+        ctx.step(q, 1000000, 0.0, T_END)
+        nsteps = ctx.get_time()[1]
+        ms = []
+        for _ in range(repeats):
+            if flush is not None:
+                flush.zero_()
+            q.copy_(q0)
+            ctx.set_time(0.0, 0)
+            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            ev[0].record()
+            ctx.step(q, nsteps, 0.0, T_END)
+            ev[1].record()
+            torch.cuda.synchronize()
+            ms.append(ev[0].elapsed_time(ev[1]))
+        avg = ctx.averages(q)[0].double().cpu().numpy()
+    err = float(np.sqrt(np.mean((avg - exact_rho_averages(nx)) ** 2)))
+    return statistics.mean(ms), nsteps, err, q
+
+
+def vortex128_case(peak):
+    """The 128^2 p = 3 vortex to t = 10 (5348 RK3 steps), FP32 and FP64: time
+    to solution, the density-average errors against the exact solution, the
+    FP32-vs-FP64 difference, and the stage kernel's roofline (its state is
+    L2-resident at this size)."""
+    import torch
+    from paper_1709_01619_gb300 import _native as nat
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ms32, n32, err32, q32 = vortex_solve(nat.F32, NX, repeats=3, flush=flush)
+    ms64, n64, err64, q64 = vortex_solve(nat.F64, NX, repeats=1, flush=flush)
+    diff = float(torch.linalg.norm(q32.double() - q64) / torch.linalg.norm(q64))
+    dof = NX * NX * (P + 1) ** 2
+    launch_ms = ms32 / (3 * n32)
+    achieved = dof * 16 * ALGO_ARRAYS_PER_STEP / 3.0 / (launch_ms * 1e-3) / 1e9
+    r64 = dof * 3 * n64 / (ms64 * 1e-3)
+    return {"workload": "euler_vortex_128x128_p3_t10", "rk3_steps": n32, "ms_fp32": ms32,
+            "dof_stage_per_s_fp32": dof * 3 * n32 / (ms32 * 1e-3), "ms_fp64": ms64,
+            "dof_stage_per_s_fp64": r64, "same_grid_f32_over_f64": ms64 / ms32,
+            "l2_rho_avg_error": {"f32": err32, "f64": err64}, "f32_vs_f64_rel_l2": diff,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                         "traffic": NCU_TRAFFIC_128, "launch_ms": launch_ms,
+                         "note": "state 4.2 MB: L2-resident, launch-latency bound"},
+            "f64_roofline": f64_roofline(r64)}
+
+
+def loglog(xs, ys, x):
+    """Piecewise-linear interpolation of log y over log x (xs decreasing or
+    increasing); None outside the range."""
+    pts = sorted(zip(xs, ys))
+    for (x0, y0), (x1, y1) in zip(pts, pts[1:]):
+        if x0 <= x <= x1:
+            if x1 == x0:
+                return y0
+            f = (math.log(x) - math.log(x0)) / (math.log(x1) - math.log(x0))
+            return math.exp(math.log(y0) + f * (math.log(y1) - math.log(y0)))
+    return None
+
+
+def time_to_error(rows, target):
+    """Least time in which a ladder of runs (dicts with 'ms' and 'err')
+    reaches error `target`: the runs that no cheaper run beats in error (the
+    time-error frontier), interpolated log-log along it; None when no run
+    reaches the target, and the cheapest run's time when it already does."""
+    front = []
+    for r in sorted(rows, key=lambda r: r["ms"]):
+        if not front or r["err"] < front[-1]["err"]:
+            front.append(r)
+    if front[0]["err"] <= target:
+        return front[0]["ms"]
+    return loglog([r["err"] for r in front], [r["ms"] for r in front], target)
+
+
+def equal_error_case(v128):
+    """Time to solution at equal error: the 128^2 p = 3 vortex to t = 10 and
+    the same problem on coarser grids (LADDER), FP32 and FP64, each with its
+    density-average error against the exact solution.  Two readings: (a) the
+    FP32 128^2 run against the FP64 time interpolated (log time over log
+    error) to its error along the FP64 ladder; (b) at given errors, the least
+    time each precision needs along its time-error frontier (FP32 stops
+    improving at its rounding floor, about 7e-7, so below that only FP64
+    reaches the error)."""
+    from paper_1709_01619_gb300 import _native as nat
+    rows = {}
+    for key, dt in (("f32", nat.F32), ("f64", nat.F64)):
+        rows[key] = []
+        for n in LADDER:
+            ms, steps, err, _ = vortex_solve(dt, n, repeats=2 if n < 96 else 1)
+            rows[key].append({"n": n, "ms": ms, "rk3_steps": steps, "err": err})
+        # the 128^2 solves of the vortex128 block
+        rows[key].append({"n": NX, "ms": v128[f"ms_{key.replace('f', 'fp')}"], "rk3_steps": v128["rk3_steps"],
+                          "err": v128["l2_rho_avg_error"][key]})
+    out = {"workload": "euler_vortex_p3_t10_grid_ladder", "ladder": rows}
+    e32 = rows["f32"][-1]["err"]
+    t32 = rows["f32"][-1]["ms"]
+    t64 = loglog([r["err"] for r in rows["f64"]], [r["ms"] for r in rows["f64"]], e32)
+    out["f32_128_run"] = {"error": e32, "f32_ms": t32, "f64_ms": t64,
+                          "speedup_f32_over_f64": (t64 / t32) if t64 else None}
+    out["frontier"] = {}
+    for target in (e32, 1e-6, 3e-6):
+        a = time_to_error(rows["f32"], target)
+        c = time_to_error(rows["f64"], target)
+        out["frontier"][f"{target:.3g}"] = {"f32_ms": a, "f64_ms": c,
+                                            "speedup_f32_over_f64": (c / a) if a and c else None}
+    return out
 
 
 def batch_case(peak, steps=100, warmup=3, tune=True):
@@ -297,7 +602,7 @@ def batch_case(peak, steps=100, warmup=3, tune=True):
     from paper_1709_01619_gb300 import inputs
     specs = inputs.batch_instances(64, seed=0)
     cfgs = [nat.Config(eqn=nat.EULER, nx=s["N"], ny=s["N"], p=s["p"], x1=L, y1=L, dtype=nat.F32,
-                       cfl={2: 0.1, 3: 0.08, 4: 0.06}[s["p"]]) for s in specs]
+                       cfl=inputs.BATCH_CFL[s["p"]]) for s in specs]
     qs = []
     for c, s in zip(cfgs, specs):
         with nat.Context(c) as ctx:
@@ -544,13 +849,16 @@ def paper_setting_case():
             "dof_stage_per_s": dof * 3 * nsteps / (ms * 1e-3), "l2_rho_avg_error": err}
 
 
-def adjoint_case():
+def adjoint_case(peak):
     """Gradient of J = 1/2 sum W (q_N - q_t)^2 with respect to the initial
     state: Euler vortex (strength 5) on [0,10]^2, 256^2, p = 3, FP32, 400
     SSP-RK3 steps of dt = 7e-4 (t = 0.28, CFL 0.07), checkpoints every 20
-    steps, q_t the forward
-    solution from strength 4.5.  Forward (with checkpoints) and backward
-    (recompute + transposed steps) timed with CUDA events."""
+    steps, q_t the forward solution from strength 4.5.  Forward (with
+    checkpoints) and backward (recompute + transposed steps) timed with CUDA
+    events.  The residual-VJP kernel alone: mean launch time at 256^2 and on
+    the 1024^2 vortex (268 MB per array, above L2), against its algorithmic
+    bytes (it reads q and the cotangent and writes the result: 3 state
+    arrays, 48 B per DOF in FP32)."""
     import torch
     from paper_1709_01619_gb300 import _native as nat
     from paper_1709_01619_gb300 import adjoint, inputs
@@ -584,25 +892,145 @@ def adjoint_case():
         fwd, bwd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
         finite = bool(torch.isfinite(g).all())
     dof = n * n * 16
+    vjp = {}
+    for m in (256, 1024):
+        c = nat.Config(eqn=nat.EULER, nx=m, ny=m, p=3, x1=L, y1=L, dtype=nat.F32)
+        with nat.Context(c) as cx:
+            x, y = cx.point_coords()
+            q = torch.tensor(inputs.vortex(x, y, eps=EPS), dtype=torch.float32, device="cuda")
+            rbar = torch.randn_like(q)
+            qbar = torch.empty_like(q)
+            reps = 50 if m == 256 else 10
+            cx.residual_vjp(q, rbar, qbar)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                cx.residual_vjp(q, rbar, qbar)
+            e1.record()
+            torch.cuda.synchronize()
+            launch = e0.elapsed_time(e1) / reps
+        achieved = m * m * 16 * 48 / (launch * 1e-3) / 1e9
+        vjp[f"{m}"] = {"launch_ms": launch, "achieved": achieved, "frac": achieved / peak}
     return {"workload": "euler_vortex_256x256_p3_fp32_adjoint_400steps_ckpt20", "forward_ms": fwd,
             "backward_ms": bwd, "gradient_ms": fwd + bwd, "backward_over_forward": bwd / fwd,
-            "forward_dof_stage_per_s": dof * 3 * nsteps / (fwd * 1e-3), "gradient_finite": finite}
+            "forward_dof_stage_per_s": dof * 3 * nsteps / (fwd * 1e-3), "gradient_finite": finite,
+            "vjp_kernel": {"bound": "hbm", "bytes_per_dof": 48, "peak": peak, "unit": "GB/s", **vjp}}
 
 
-def run_hbm_only(args):
+def run_cpr(args, world, rank, local):
+    peak, peak_kind = peaks()
+    head = batch_headline(args, world, local, peak)
+    cfg = {"workload": WORKLOAD, "instances": BATCH_N, "seed": BATCH_SEED,
+           "N": "U{32..256}", "p": "U{2,3,4}", "strength": "U[1,5]", "dof": head["dof"],
+           "rk3_steps_per_pass": BATCH_STEPS, "cfl": "0.1/0.06/0.04 (p=2/3/4)", "points": "gauss",
+           "flux": "rusanov", "form": "per-instance chains" if head["per_instance"] else "grouped launches",
+           "l2_flush": "inputs larger than L2 (445 MB per state array; states reset before each pass, "
+                       "outside the timed events)", "replicas": world}
+    line = {
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_max"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+        "roofline": {**head["roofline"], "peak_source": peak_kind},
+        "e2e": {"value": head["e2e"], "unit": UNIT, "h2d_bytes_per_step": head["state_bytes"],
+                "d2h_bytes_per_step": head["state_bytes"]},
+        "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
+    }
+    detail = {"headline": {k: head[k] for k in ("tuned", "per_instance", "steps_done", "t_min", "t_max",
+                                                "finite", "e2e_equal")}}
+    if args.quick:
+        if rank == 0:
+            print(json.dumps(compact(line)), flush=True)
+        return
     import torch
-    from paper_1709_01619_gb300 import _native as nat
-    from paper_1709_01619_gb300 import inputs
+
+    def mk(dtype, nx, p=P):
+        return make_vortex(dtype, nx, p)
+
+    side = {}
+    side["hbm1024"] = hbm_case(mk, peak)
+    v128 = vortex128_case(peak)
+    side["vortex128"] = v128
+    side["equal_error"] = equal_error_case(v128)
+    side["limited"] = limited_case(peak)
+    fv = fv_case(peak)
+    fv["cpr_512_p2_over_fv_time_to_solution"] = side["limited"]["ms_fp32"] / fv["ms_fp32"]
+    side["fv_equal_dof"] = fv
+    side["radial_shock_tube"] = radial_case()
+    side["adjoint"] = adjoint_case(peak)
+    side["paper_setting"] = paper_setting_case()
+    torch.cuda.synchronize()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        states = oracle_batch_states()
+        v, work, secs, thr = oracle_batch_sample(1, states=states)
+        sub = states[::4]
+        v1, work1, secs1, _ = oracle_batch_sample(1, threads=1, states=sub)
+        cpu = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"1 FP64 SSP-RK3 CFL step of all 64 instances ({work:.3g} DOF-stages, {secs:.1f} s)",
+               "single_thread": {"value": v1, "sample": f"1 step of every 4th instance ({secs1:.1f} s)"},
+               "cpu": cpu_model()}
+    line["cpu_baseline"] = cpu
+    if rank != 0:
+        return
+    h, v, e, lim, fvq, rad, adj = (side["hbm1024"], side["vortex128"], side["equal_error"], side["limited"],
+                                   side["fv_equal_dof"], side["radial_shock_tube"], side["adjoint"])
+    # compact side blocks on the line itself; full records on stderr
+    line["hbm1024"] = {"frac": h["frac"], "moved_frac": h["moved_frac"], "launch_ms": h["launch_ms"],
+                       "traffic": h["traffic"], "rate": h["dof_stage_per_s"]}
+    line["vortex128"] = {"f32_rate": v["dof_stage_per_s_fp32"], "f64_rate": v["dof_stage_per_s_fp64"],
+                         "same_grid_f32_over_f64": v["same_grid_f32_over_f64"],
+                         "err_f32": v["l2_rho_avg_error"]["f32"], "err_f64": v["l2_rho_avg_error"]["f64"],
+                         "f32_vs_f64": v["f32_vs_f64_rel_l2"], "frac": v["roofline"]["frac"],
+                         "f64_alu_frac": v["f64_roofline"]["frac"],
+                         "f64_alu_frac_executed": v["f64_roofline"]["executed_frac"]}
+    fr = e["frontier"]
+    line["equal_error_speedup"] = {
+        "error": e["f32_128_run"]["error"],
+        "f32_128_run_vs_f64_interp": e["f32_128_run"]["speedup_f32_over_f64"],
+        "frontier_at_f32_128_error": fr[f"{e['f32_128_run']['error']:.3g}"]["speedup_f32_over_f64"],
+        "frontier_at_1e-6": fr["1e-06"]["speedup_f32_over_f64"],
+        "frontier_at_3e-6": fr["3e-06"]["speedup_f32_over_f64"]}
+    line["limited"] = {"ms_f32": lim["ms_fp32"], "rate_f32": lim["dof_stage_per_s_fp32"], "frac": lim["frac"],
+                       "rate_f64": lim["dof_stage_per_s_fp64"], "f32_vs_f64": lim.get("f32_vs_f64_rel_l2")}
+    line["fv"] = {"ms_muscl2": fvq["ms_fp32"], "ms_muscl3": fvq["muscl3"]["ms_fp32"],
+                  "cpr_over_fv_time": fvq["cpr_512_p2_over_fv_time_to_solution"]}
+    line["radial"] = {"cpr_ms": rad["cpr_400_p2"]["ms"], "fv2_ms": rad["fv_muscl2_1200"]["ms"],
+                      "fv3_ms": rad["fv_muscl3_1200"]["ms"]}
+    line["adjoint"] = {"fwd_ms": adj["forward_ms"], "bwd_ms": adj["backward_ms"],
+                       "vjp_frac_1024": adj["vjp_kernel"]["1024"]["frac"],
+                       "vjp_ms_256": adj["vjp_kernel"]["256"]["launch_ms"]}
+    line["paper_setting"] = {"rate": side["paper_setting"]["dof_stage_per_s"],
+                             "err": side["paper_setting"]["l2_rho_avg_error"]}
+    detail.update(side)
+    detail["cpu_baseline"] = cpu
+    print(json.dumps(compact(detail, 6)), file=sys.stderr, flush=True)
+    print(json.dumps(compact(line)), flush=True)
+
+
+def run_block(args):
+    """--workload other than headline: one block alone (profiling runs)."""
     peak, _ = peaks()
-
-    def make(dtype, nx):
-        cfg = nat.Config(eqn=nat.EULER, nx=nx, ny=nx, p=P, x1=L, y1=L, cfl=CFL, dtype=dtype)
-        ctx = nat.Context(cfg)
-        x, y = ctx.point_coords()
-        q0 = torch.tensor(inputs.vortex(x, y, eps=EPS), dtype=cfg.torch_dtype, device="cuda")
-        return cfg, ctx, q0
-
-    print(json.dumps(hbm_case(make, peak, max(1, args.steps))), flush=True)
+    w = args.workload
+    if w == "vortex1024":
+        out = hbm_case(make_vortex, peak, max(1, args.steps), args.p)
+    elif w == "batch":
+        out = batch_case(peak, steps=max(1, args.steps), warmup=args.warmup, tune=not args.no_tune)
+    elif w == "limited":
+        out = limited_case(peak, fp64_steps=max(1, args.steps))
+    elif w == "radial":
+        out = radial_case()
+    elif w == "fv1536":
+        out = fv_case(peak, fp64_steps=max(1, args.steps))
+    elif w == "vortex128":
+        out = vortex128_case(peak)
+    elif w == "ladder":
+        out = equal_error_case(vortex128_case(peak))
+    elif w == "adjoint":
+        out = adjoint_case(peak)
+    else:  # f64
+        out = run_f64_only(args)
+    print(json.dumps(compact(out, 6)), flush=True)
 
 
 def run_f64_only(args):
@@ -610,11 +1038,8 @@ def run_f64_only(args):
     three untimed ones (a short run for profiling the FP64 stage kernel)."""
     import torch
     from paper_1709_01619_gb300 import _native as nat
-    from paper_1709_01619_gb300 import inputs
-    cfg = nat.Config(eqn=nat.EULER, nx=NX, ny=NX, p=P, x1=L, y1=L, cfl=CFL, dtype=nat.F64)
-    with nat.Context(cfg) as ctx:
-        x, y = ctx.point_coords()
-        q = torch.tensor(inputs.vortex(x, y, eps=EPS), dtype=torch.float64, device="cuda")
+    cfg, ctx, q = make_vortex(nat.F64, NX, P)
+    with ctx:
         ctx.step(q, 3)
         torch.cuda.synchronize()
         ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -625,153 +1050,8 @@ def run_f64_only(args):
         ms = ev[0].elapsed_time(ev[1])
     dof = NX * NX * (P + 1) ** 2
     rate = dof * 3 * args.steps / (ms * 1e-3)
-    print(json.dumps({"workload": "euler_vortex_128x128_p3_fp64", "rk3_steps": args.steps, "ms": ms,
-                      "dof_stage_per_s": rate, **f64_roofline(rate)}), flush=True)
-
-
-def run_cpr(args, world, rank, local):
-    import torch
-    from paper_1709_01619_gb300 import _native as nat
-    from paper_1709_01619_gb300 import inputs
-
-    dof = NX * NX * (P + 1) ** 2
-    peak, peak_kind = peaks()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-
-    def make(dtype, nx=NX):
-        cfg = nat.Config(eqn=nat.EULER, nx=nx, ny=nx, p=P, x1=L, y1=L, cfl=CFL, dtype=dtype)
-        ctx = nat.Context(cfg)
-        x, y = ctx.point_coords()
-        q0 = torch.tensor(inputs.vortex(x, y, eps=EPS), dtype=cfg.torch_dtype, device="cuda")
-        return cfg, ctx, q0
-
-    def solve(ctx, q, q0, nsteps, ev=None):
-        flush.zero_()
-        q.copy_(q0)
-        ctx.set_time(0.0, 0)
-        if ev:
-            ev[0].record()
-        ctx.step(q, nsteps, 0.0, T_END)
-        if ev:
-            ev[1].record()
-
-    # ---- FP32 (headline) ----------------------------------------------------
-    cfg32, ctx32, q0_32 = make(nat.F32)
-    q32 = torch.empty_like(q0_32)
-    solve(ctx32, q32, q0_32, 20000)
-    nsteps = ctx32.get_time()[1]
-    for _ in range(max(0, args.warmup - 1)):
-        solve(ctx32, q32, q0_32, nsteps)
-    torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    barrier(world)
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        solve(ctx32, q32, q0_32, nsteps, evs[k])
-    torch.cuda.synchronize()
-    barrier(world)
-    clk = clocks.stop()
-    ms = sum(a.elapsed_time(b) for a, b in evs)
-    t_fin, steps_fin = ctx32.get_time()
-    ms_max = max_over_ranks(ms, world)
-    updates = dof * 3 * nsteps * args.steps
-    value = sum_over_ranks(updates, world) / (ms_max * 1e-3)
-    avg32 = ctx32.averages(q32)[0].double().cpu().numpy()
-
-    # dominant kernel: fused residual + stage, 3 launches per RK3 step
-    launch_ms = ms / (args.steps * 3 * nsteps)
-    bytes_per_launch = dof * 4 * 4 * ALGO_ARRAYS_PER_STEP / 3.0
-    achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
-
-    if args.quick:
-        if rank == 0:
-            print(json.dumps({"workload": "euler_vortex_128x128_p3_t10", "value": value, "unit": UNIT,
-                              "ms_per_step": ms_max / args.steps, "rk3_steps": nsteps,
-                              "launch_ms": launch_ms}), flush=True)
-        return
-
-    # ---- e2e through the host-buffer entry point ------------------------------
-    qh_in = q0_32.cpu().pin_memory()
-    qh_out = torch.empty_like(qh_in).pin_memory()
-    ctx32.set_time(0.0, 0)
-    ctx32.step_host(qh_in, qh_out, nsteps, 0.0, T_END)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        ctx32.set_time(0.0, 0)
-        ctx32.step_host(qh_in, qh_out, nsteps, 0.0, T_END)
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
-    e2e = sum_over_ranks(updates, world) / e2e_s
-    state_bytes = qh_in.numel() * 4
-
-    # ---- FP64 path, same solve ----------------------------------------------
-    cfg64, ctx64, q0_64 = make(nat.F64)
-    q64 = torch.empty_like(q0_64)
-    solve(ctx64, q64, q0_64, nsteps + 100)
-    n64 = ctx64.get_time()[1]
-    ev64 = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-    solve(ctx64, q64, q0_64, n64, ev64)
-    torch.cuda.synchronize()
-    ms64 = ev64[0].elapsed_time(ev64[1])
-    avg64 = ctx64.averages(q64)[0].cpu().numpy()
-    exact = exact_rho_averages(NX)
-    err32 = float(np.sqrt(np.mean((avg32 - exact) ** 2)))
-    err64 = float(np.sqrt(np.mean((avg64 - exact) ** 2)))
-    diff = float(np.linalg.norm(q32.double().cpu().numpy() - q64.cpu().numpy()) /
-                 np.linalg.norm(q64.cpu().numpy()))
-    value64 = dof * 3 * n64 / (ms64 * 1e-3)
-    del ctx64
-
-    hbm = hbm_case(make, peak)
-    batch = batch_case(peak)
-    limited = limited_case(peak)
-    fv = fv_case(peak)
-    fv["cpr_512_p2_over_fv_time_to_solution"] = limited["ms_fp32"] / fv["ms_fp32"]
-    radial = radial_case()
-    adj = adjoint_case()
-    paper = paper_setting_case()
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, s, secs, thr = oracle_sample(12.0)
-        cpu = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
-               "sample": f"{s} FP64 SSP-RK3 steps of the same 128x128 p=3 vortex ({secs:.1f} s)"}
-
-    if rank != 0:
-        return
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "euler_vortex_128x128_p3_t10", "nx": NX, "ny": NX, "p": P,
-                   "points": "gauss", "flux": "rusanov", "t_end": T_END, "cfl": CFL,
-                   "rk3_steps_per_solve": nsteps, "t_reached": t_fin,
-                   "l2_flush": "256 MiB write before every timed solve",
-                   "replicas": world},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": NCU_TRAFFIC_128, "peak_source": peak_kind,
-                     "kernel": "cpr_stage_kernel<float,3,Euler,LP,Rusanov> (two-CTA-per-SM instantiation)",
-                     "bytes_per_launch": bytes_per_launch,
-                     "note": "state (4.2 MB) is L2-resident at this size; traffic from a cold ncu replay"},
-        "roofline_hbm_case": hbm,
-        "batch": batch,
-        "limited": limited,
-        "fv_equal_dof": fv,
-        "radial_shock_tube": radial,
-        "adjoint": adj,
-        "paper_setting": paper,
-        "f64": {"value": value64, "unit": UNIT, "ms_per_solve": ms64, "rk3_steps": n64,
-                "roofline": f64_roofline(value64)},
-        "l2_rho_avg_error": {"f32": err32, "f64": err64},
-        "f32_vs_f64_rel_l2": diff,
-        "speedup_f32_over_f64": value / world / value64 if value64 > 0 else None,
-        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
-                "d2h_bytes_per_step": state_bytes},
-        "gpu_launches": args.steps * (3 * nsteps + 3),
-        "clocks": clk,
-        "cpu_baseline": cpu,
-    }
-    print(json.dumps(line), flush=True)
+    return {"workload": "euler_vortex_128x128_p3_fp64", "rk3_steps": args.steps, "ms": ms,
+            "dof_stage_per_s": rate, **f64_roofline(rate)}
 
 
 def main():
@@ -779,21 +1059,10 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
-    elif args.workload == "vortex1024":
-        run_hbm_only(args)
-    elif args.workload == "batch":
-        print(json.dumps(batch_case(peaks()[0], steps=max(1, args.steps), warmup=args.warmup,
-                                    tune=not args.no_tune)), flush=True)
-    elif args.workload == "limited":
-        print(json.dumps(limited_case(peaks()[0], fp64_steps=max(1, args.steps))), flush=True)
-    elif args.workload == "radial":
-        print(json.dumps(radial_case()), flush=True)
-    elif args.workload == "f64":
-        run_f64_only(args)
-    elif args.workload == "fv1536":
-        print(json.dumps(fv_case(peaks()[0], fp64_steps=max(1, args.steps))), flush=True)
-    else:
+    elif args.workload == "headline":
         run_cpr(args, world, rank, local)
+    else:
+        run_block(args)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
