@@ -32,14 +32,22 @@ class CPRRollout(torch.autograd.Function):
         solver, nsteps, dt, every = ctx.solver, ctx.nsteps, ctx.dt, ctx.every
         qbar = gout.contiguous().clone()
         tmp = torch.empty_like(qbar)
+        # One work array for the recomputation and one buffer per state of a
+        # segment, allocated once: the context's step graphs are bound to the
+        # state array they step, so a fixed work array keeps them across the
+        # segments (a fresh array per segment would re-capture them).
+        work = torch.empty_like(qbar)
+        bufs = [torch.empty_like(qbar) for _ in range(min(every, nsteps) - 1)]
         for k in reversed(range(len(ctx.ckpts))):
             start = k * every
             end = min(start + every, nsteps)
             states = [ctx.ckpts[k]]
-            q = ctx.ckpts[k].clone()
-            for _ in range(start, end - 1):
-                solver.step(q, 1, dt)
-                states.append(q.clone())
+            work.copy_(ctx.ckpts[k])
+            for s in range(start, end - 1):
+                solver.step(work, 1, dt)
+                b = bufs[s - start]
+                b.copy_(work)
+                states.append(b)
             for s in reversed(range(end - start)):
                 solver.step_vjp(states[s], qbar, dt, tmp)
                 qbar, tmp = tmp, qbar

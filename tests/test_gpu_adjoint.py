@@ -147,15 +147,16 @@ def test_config5_gradient_full_size_vs_fp64_differences():
     checkpoints every 20 steps; q_t is the forward solution from the vortex
     of strength 4.5.
 
-    (1) The FP64 adjoint gradient projected on 16 random Gaussian directions d
-    against central differences of J (h = 1e-4) from the FP64 solver.  With
-    4.2 million entries a projection cancels by three to five orders of
-    magnitude, so the error is measured on the scale of the projection,
-    |g.d - fd| / (|g| |d|): the O(h^2) truncation of the difference keeps it
-    near 1e-9 (at most 3.4e-9 seen); bound 1e-8.
-    (2) The FP32 adjoint gradient against the FP64 one, relative L2 over the
-    whole vector: FP32 rounding accumulated over 1200 stages and their
-    adjoints (5.4e-5 seen); bound 2e-4."""
+    (1) The FP64 adjoint gradient g projected on 32 random Gaussian
+    directions d against central differences of J (h = 1e-4) from the FP64
+    solver.  For unit-variance Gaussian d the projection g.d has standard
+    deviation |g|, its natural scale: the error |g.d - fd| stays below
+    2e-5 |g| (the O(h^2) truncation), and below 1e-4 |g.d| wherever the
+    projection is not close to zero (|g.d| > 0.2 |g|).
+    (2) The FP32 adjoint gradient: its projections against the same FP64
+    central differences (FP32 rounding accumulated over 1200 stages and
+    their adjoints: within 3e-4 |g|), and against the FP64 gradient, relative
+    L2 over the whole vector (5.4e-5 seen; bound 2e-4)."""
     n, nsteps, dt = 256, 400, 7e-4
     c32 = nat.Config(dtype=nat.F32, eqn=nat.EULER, nx=n, ny=n, p=3, x1=10.0, y1=10.0)
     c64 = nat.Config(dtype=nat.F64, eqn=nat.EULER, nx=n, ny=n, p=3, x1=10.0, y1=10.0)
@@ -185,8 +186,15 @@ def test_config5_gradient_full_size_vs_fp64_differences():
 
         rng = np.random.default_rng(5)
         h = 1e-4
-        for _ in range(16):
+        gn = float(g64.norm())
+        big = 0
+        for _ in range(32):
             d = torch.tensor(rng.standard_normal(c64.shape), device="cuda")
             fd = (J64(q0 + h * d) - J64(q0 - h * d)) / (2 * h)
-            scale = float(g64.norm() * d.norm())
-            assert abs(float((g64 * d).sum()) - fd) <= 1e-8 * scale
+            p64 = float((g64 * d).sum())
+            assert abs(p64 - fd) <= 2e-5 * gn
+            if abs(p64) > 0.2 * gn:
+                big += 1
+                assert abs(p64 - fd) <= 1e-4 * abs(p64)
+            assert abs(float((g32 * d).sum()) - fd) <= 3e-4 * gn
+        assert big >= 16  # most projections are not near zero
