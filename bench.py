@@ -103,10 +103,12 @@ def parse():
     ap.add_argument("--impl", choices=["cpr", "reference"], default="cpr")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["headline", "vortex128", "vortex1024", "batch", "fv1536", "limited",
-                                           "radial", "f64", "ladder", "adjoint"],
+                                           "radial", "f64", "ladder", "adjoint", "vjp"],
                     default="headline", help="anything but headline: only that block (short runs for "
                     "profiling)")
     ap.add_argument("--p", type=int, default=P, help="--workload vortex1024: the order")
+    ap.add_argument("--per-instance", action="store_true",
+                    help="--workload batch --no-tune: the per-instance chains instead of grouped launches")
     ap.add_argument("--no-tune", action="store_true",
                     help="--workload batch: the untuned launch (for profilers, whose serialised replays "
                     "distort the autotuner's timings)")
@@ -590,12 +592,13 @@ def equal_error_case(v128):
     return out
 
 
-def batch_case(peak, steps=100, warmup=3, tune=True):
+def batch_case(peak, steps=100, warmup=3, tune=True, per_instance=False):
     """64 isentropic-vortex instances (N ~ U{32..256}, p ~ U{2,3,4}, strength
     ~ U[1,5], numpy seed 0) on [0,10]^2 in FP32, advanced together by the
     batched solver with per-instance CFL steps after autotuning (tune=False:
-    the untuned launch, the grouped form with one CTA per tile of the 8x8
-    family, for profilers, whose serialised replays would distort the
+    untuned, the grouped form with one CTA per tile of the 8x8 family, or
+    with per_instance the per-instance chains, the form the autotuner picks
+    on GB300; for profilers, whose serialised replays would distort the
     autotuner's timings)."""
     import torch
     from paper_1709_01619_gb300 import _native as nat
@@ -611,6 +614,8 @@ def batch_case(peak, steps=100, warmup=3, tune=True):
     dof = sum(c.nx * c.ny * (c.p + 1) ** 2 for c in cfgs)
     with nat.Batch(cfgs) as b:
         choices = b.tune(qs) if tune else []
+        if not tune and per_instance:
+            b.set_form(True)
         b.step(qs, warmup)
         torch.cuda.synchronize()
         ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -632,8 +637,9 @@ def limited_case(peak, fp64_steps=None):
     elements, p = 2, TVB minmod limiter (M = 50, eps = 1e-3) after every RK
     stage, transmissive boundaries, CFL 0.1: the FP32 solve to t = 0.3 timed
     whole (the initial condition limited once, outside the timing); FP64 the
-    same solve to t = 0.3 (or fp64_steps CFL steps, for short profiling
-    runs), and the FP32-vs-FP64 relative L2 difference of the final states."""
+    same solve to t = 0.3, and the FP32-vs-FP64 relative L2 difference of the
+    final states.  fp64_steps: only that many CFL steps in both precisions
+    (short runs for profiling)."""
     import torch
     from paper_1709_01619_gb300 import _native as nat
     from paper_1709_01619_gb300 import inputs
@@ -651,9 +657,12 @@ def limited_case(peak, fp64_steps=None):
     dof = nx * nx * (p + 1) ** 2
     ctx, q0 = make(nat.F32)
     q = q0.clone()
-    ctx.set_time(0.0, 0)
-    ctx.step(q, 100000, 0.0, t_end)
-    nsteps = ctx.get_time()[1]
+    if fp64_steps:
+        nsteps = fp64_steps  # a short run of both precisions (profiling)
+    else:
+        ctx.set_time(0.0, 0)
+        ctx.step(q, 100000, 0.0, t_end)
+        nsteps = ctx.get_time()[1]
     q.copy_(q0)
     ctx.set_time(0.0, 0)
     torch.cuda.synchronize()
@@ -849,6 +858,34 @@ def paper_setting_case():
             "dof_stage_per_s": dof * 3 * nsteps / (ms * 1e-3), "l2_rho_avg_error": err}
 
 
+def vjp_case(peak, reps=10, n=1024):
+    """The residual-VJP kernel alone on the n^2 p = 3 FP32 vortex (1024^2:
+    268 MB per state array, above L2): mean time of `reps` launches after one
+    untimed launch, against its algorithmic bytes (reads q and the cotangent,
+    writes the result: 3 state arrays, 48 B per DOF)."""
+    import torch
+    from paper_1709_01619_gb300 import _native as nat
+    from paper_1709_01619_gb300 import inputs
+    c = nat.Config(eqn=nat.EULER, nx=n, ny=n, p=3, x1=L, y1=L, dtype=nat.F32)
+    with nat.Context(c) as cx:
+        x, y = cx.point_coords()
+        q = torch.tensor(inputs.vortex(x, y, eps=EPS), dtype=torch.float32, device="cuda")
+        rbar = torch.tensor(inputs.noise(tuple(q.shape), 11, 1.0), dtype=torch.float32, device="cuda")
+        qbar = torch.empty_like(q)
+        cx.residual_vjp(q, rbar, qbar)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            cx.residual_vjp(q, rbar, qbar)
+        e1.record()
+        torch.cuda.synchronize()
+        launch = e0.elapsed_time(e1) / reps
+    achieved = n * n * 16 * 48 / (launch * 1e-3) / 1e9
+    return {"workload": f"euler_vortex_{n}x{n}_p3_fp32_residual_vjp", "launch_ms": launch, "bound": "hbm",
+            "bytes_per_dof": 48, "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak}
+
+
 def adjoint_case(peak):
     """Gradient of J = 1/2 sum W (q_N - q_t)^2 with respect to the initial
     state: Euler vortex (strength 5) on [0,10]^2, 256^2, p = 3, FP32, 400
@@ -892,26 +929,7 @@ def adjoint_case(peak):
         fwd, bwd = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
         finite = bool(torch.isfinite(g).all())
     dof = n * n * 16
-    vjp = {}
-    for m in (256, 1024):
-        c = nat.Config(eqn=nat.EULER, nx=m, ny=m, p=3, x1=L, y1=L, dtype=nat.F32)
-        with nat.Context(c) as cx:
-            x, y = cx.point_coords()
-            q = torch.tensor(inputs.vortex(x, y, eps=EPS), dtype=torch.float32, device="cuda")
-            rbar = torch.randn_like(q)
-            qbar = torch.empty_like(q)
-            reps = 50 if m == 256 else 10
-            cx.residual_vjp(q, rbar, qbar)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(reps):
-                cx.residual_vjp(q, rbar, qbar)
-            e1.record()
-            torch.cuda.synchronize()
-            launch = e0.elapsed_time(e1) / reps
-        achieved = m * m * 16 * 48 / (launch * 1e-3) / 1e9
-        vjp[f"{m}"] = {"launch_ms": launch, "achieved": achieved, "frac": achieved / peak}
+    vjp = {f"{m}": vjp_case(peak, 50 if m == 256 else 10, m) for m in (256, 1024)}
     return {"workload": "euler_vortex_256x256_p3_fp32_adjoint_400steps_ckpt20", "forward_ms": fwd,
             "backward_ms": bwd, "gradient_ms": fwd + bwd, "backward_over_forward": bwd / fwd,
             "forward_dof_stage_per_s": dof * 3 * nsteps / (fwd * 1e-3), "gradient_finite": finite,
@@ -1015,7 +1033,8 @@ def run_block(args):
     if w == "vortex1024":
         out = hbm_case(make_vortex, peak, max(1, args.steps), args.p)
     elif w == "batch":
-        out = batch_case(peak, steps=max(1, args.steps), warmup=args.warmup, tune=not args.no_tune)
+        out = batch_case(peak, steps=max(1, args.steps), warmup=args.warmup, tune=not args.no_tune,
+                         per_instance=args.per_instance)
     elif w == "limited":
         out = limited_case(peak, fp64_steps=max(1, args.steps))
     elif w == "radial":
@@ -1028,6 +1047,8 @@ def run_block(args):
         out = equal_error_case(vortex128_case(peak))
     elif w == "adjoint":
         out = adjoint_case(peak)
+    elif w == "vjp":
+        out = vjp_case(peak, max(1, args.steps))
     else:  # f64
         out = run_f64_only(args)
     print(json.dumps(compact(out, 6)), flush=True)

@@ -46,11 +46,6 @@
 #include "cpr_common.cuh"
 #include "cpr_reduce.cuh"
 
-// FP32 p = 4: rows of the tile copy padded to 8 words (1) or packed (0).
-#ifndef CPR_STAGE_PAD5
-#define CPR_STAGE_PAD5 0
-#endif
-
 namespace cpr {
 
 template <class T>
@@ -85,11 +80,7 @@ struct StageLayout {
     // row reads of a warp are conflict-free, column reads at most two-way);
     // N = 2: stride 6 (rows of 8 bytes stay aligned).
     static constexpr bool SWZ = N == 4;
-    // N = 5 in the padded form: rows of 8 words (16-byte aligned, one
-    // 16-byte and one 4-byte access per row), elements of 40 words
-    static constexpr bool PAD5 = N == 5 && CPR_STAGE_PAD5 != 0 && !DELTA;
-    static constexpr int RS = PAD5 ? 8 : N;
-    static constexpr int ES = SWZ ? 16 : (N == 2 ? 6 : N * RS);
+    static constexpr int ES = SWZ ? 16 : (N == 2 ? 6 : NN);
     static constexpr int E = TX * TY;
     static constexpr int PE = (TX + 2) * (TY + 2);     // tile with its halo ring
     // The y-derivatives go over the dead tile copy in phase 3 (a buffer of
@@ -110,7 +101,7 @@ struct StageLayout {
     // point (b, a) (row b, column a) of element el in a tile array
     __device__ static int sq(int v, int el, int b, int a)
     {
-        return (v * E + el) * ES + (SWZ ? 4 * (b ^ ((el >> 1) & 3)) : b * RS) + a;
+        return (v * E + el) * ES + (SWZ ? 4 * (b ^ ((el >> 1) & 3)) : b * N) + a;
     }
     __device__ static int xr(int v, int ty, int f, int k) { return ((v * TY + ty) * (TX + 1) + f) * N + k; }
     __device__ static int xh(int v, int ty, int k) { return (v * TY + ty) * N + k; }
@@ -170,29 +161,24 @@ __device__ __forceinline__ void gstore_row(T* __restrict__ d, const T* x)
     }
 }
 
-// Row of N values of one variable in shared memory (16-byte aligned when N = 4,
-// or N = 5 with A16).
-template <int N, bool A16 = false, class T>
+// Row of N values of one variable in shared memory (16-byte aligned when N = 4).
+template <int N, class T>
 __device__ __forceinline__ void sm_store_row(T* d, const T* x)
 {
     if constexpr (sizeof(T) == 4 && N == 4) {
         *reinterpret_cast<float4*>(d) = make_float4(x[0], x[1], x[2], x[3]);
-    } else if constexpr (sizeof(T) == 4 && N == 5 && A16) {
-        *reinterpret_cast<float4*>(d) = make_float4(x[0], x[1], x[2], x[3]);
-        d[4] = x[4];
     } else {
 #pragma unroll
         for (int a = 0; a < N; ++a) d[a] = x[a];
     }
 }
 
-template <int N, bool A16 = false, class T>
+template <int N, class T>
 __device__ __forceinline__ void sm_load_row(const T* s, T* x)
 {
-    if constexpr (sizeof(T) == 4 && (N == 4 || (N == 5 && A16))) {
+    if constexpr (sizeof(T) == 4 && N == 4) {
         float4 t = *reinterpret_cast<const float4*>(s);
         x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
-        if constexpr (N == 5) x[4] = s[4];
     } else {
 #pragma unroll
         for (int a = 0; a < N; ++a) x[a] = s[a];
@@ -430,7 +416,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
 #pragma unroll
                 for (int a = 0; a < N; ++a) row[a] += b[a];
             }
-            sm_store_row<N, L::PAD5>(sq + L::sq(v, el, k, 0), row);
+            sm_store_row<N>(sq + L::sq(v, el, k, 0), row);
             q0[v] = T(0);
             if (DELTA) {
                 // point (0, 0) of the element, formed exactly as the halo
@@ -583,7 +569,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
     // conflict; the element-major identity would put two elements' columns
     // in one bank.  Even N: the row identity (the N = 4 swizzle makes both
     // access patterns conflict-free for it).
-    constexpr bool KMAJ = (N % 2 == 1) && !DELTA && !L::PAD5;
+    constexpr bool KMAJ = (N % 2 == 1) && !DELTA;
     const int elc = KMAJ ? tid % (TX * TY) : el, kc = KMAJ ? tid / (TX * TY) : k;
     const int txc = elc % TX, tyc = elc / TX;
     const bool validc = active && txc < TXe && tyc < TYe;
@@ -777,7 +763,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             T acc[N], jb[N], jt[N];
-            sm_load_row<N, L::PAD5>(ryS + L::sq(v, el, k, 0), acc);
+            sm_load_row<N>(ryS + L::sq(v, el, k, 0), acc);
             sm_load_row<N>(jB + L::ef(v, el, 0), jb);
             sm_load_row<N>(yF + L::ef(v, el, 0), jt);
             const T JR = xF[L::ef(v, el, k)];
