@@ -58,19 +58,33 @@ inline long long current_l2_bytes()
     return 0;
 }
 
-// Element tile of one stage-kernel CTA (compile-time; overridable for tuning
-// sweeps with -DCPR_TILE_X=.. -DCPR_TILE_Y=..).
+// Element tile of one stage-kernel CTA per order (compile-time; overridable
+// for tuning sweeps with -DCPR_TILE_X=.., -DCPR_TILE_Y=.., -DCPR_TILE_X_P4=..,
+// -DCPR_TILE_Y_P4=..):
+// 8 x 8 elements, and 8 x 4 for p = 4, whose 160-thread CTAs keep the
+// threads per SM of 320-thread ones (the register budget scales with the
+// tile) while twice as many CTAs per SM hide each other's barriers (820^2
+// p = 4: 328 -> 306 us per stage launch; 8 x 4 tiles for p = 2 and 3 were
+// slower, 308 -> 339 and 216 -> 230 us).
 #ifndef CPR_TILE_X
 #define CPR_TILE_X 8
 #endif
 #ifndef CPR_TILE_Y
 #define CPR_TILE_Y 8
 #endif
-constexpr int kTileX = CPR_TILE_X, kTileY = CPR_TILE_Y;
+#ifndef CPR_TILE_X_P4
+#define CPR_TILE_X_P4 CPR_TILE_X
+#endif
+#ifndef CPR_TILE_Y_P4
+#define CPR_TILE_Y_P4 4
+#endif
+constexpr int stage_tile_x(int p) { return p == 4 ? CPR_TILE_X_P4 : CPR_TILE_X; }
+constexpr int stage_tile_y(int p) { return p == 4 ? CPR_TILE_Y_P4 : CPR_TILE_Y; }
 
 inline int stage_ctas(const LaunchCfg& c)
 {
-    return ((c.nx + kTileX - 1) / kTileX) * ((c.ny + kTileY - 1) / kTileY);
+    const int tx = stage_tile_x(c.p), ty = stage_tile_y(c.p);
+    return ((c.nx + tx - 1) / tx) * ((c.ny + ty - 1) / ty);
 }
 
 // Buffers of one stage launch (see the modes of cpr_stage.cuh): qs the stage

@@ -332,13 +332,19 @@ constexpr bool stage_delta()
 #ifndef CPR_STAGE_MINB_WIDE
 #define CPR_STAGE_MINB_WIDE 2
 #endif
-template <class T, int N, bool WIDE = false>
+// The counts are for tiles of 64 elements; a smaller tile (ELEMS elements)
+// takes proportionally more CTAs, so that the threads per SM and the
+// registers per thread stay the same.
+template <class T, int N, bool WIDE = false, int ELEMS = 64>
 constexpr int stage_min_blocks()
 {
-    return sizeof(T) == 8 ? 1
-           : WIDE         ? CPR_STAGE_MINB_WIDE
-                          : (N == 2 ? CPR_STAGE_MINB_FP32_N2
-                                    : (N == 3 ? CPR_STAGE_MINB_FP32_N3 : (N == 4 ? CPR_STAGE_MINB_FP32 : CPR_STAGE_MINB_FP32_N5)));
+    static_assert(64 % ELEMS == 0, "tiles of 64 elements or a divisor of it");
+    return (64 / ELEMS) *
+           (sizeof(T) == 8 ? 1
+            : WIDE         ? CPR_STAGE_MINB_WIDE
+                           : (N == 2 ? CPR_STAGE_MINB_FP32_N2
+                                     : (N == 3 ? CPR_STAGE_MINB_FP32_N3
+                                               : (N == 4 ? CPR_STAGE_MINB_FP32 : CPR_STAGE_MINB_FP32_N5))));
 }
 
 // One tile of the stage: the work of one CTA.  tile indexes the instance's
@@ -886,7 +892,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
 // PF: the instantiation for compensated stages whose states exceed L2 (it
 // prefetches the low part; launched only when StageArgs::pf_lo is set).
 template <class T, int P, int EQ, int DIV, int FLUX, int TX, int TY, bool DELTA, bool PF = false, bool WIDE = false>
-__global__ void __launch_bounds__(TX * TY * (P + 1), (stage_min_blocks<T, P + 1, WIDE>()))
+__global__ void __launch_bounds__(TX * TY * (P + 1), (stage_min_blocks<T, P + 1, WIDE, TX * TY>()))
 cpr_stage_kernel(const StageArgs<T> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -15,17 +15,21 @@ template <class T, int P, int EQ, int DIV, int FLUX>
 static cudaError_t stage_one(const LaunchCfg& c, const StageArgs<T>& A, int ctas, cudaStream_t s, bool prep)
 {
     constexpr int N = P + 1, V = NVars<EQ>::value;
-    constexpr int NT = kTileX * kTileY * N;
-    const size_t smem = sizeof(T) * StageLayout<N, V, kTileX, kTileY, stage_delta<T>()>::TOTAL;
-    auto kern = cpr_stage_kernel<T, P, EQ, DIV, FLUX, kTileX, kTileY, stage_delta<T>()>;
+    constexpr int TX = stage_tile_x(P), TY = stage_tile_y(P);
+    constexpr int NT = TX * TY * N;
+    const size_t smem = sizeof(T) * StageLayout<N, V, TX, TY, stage_delta<T>()>::TOTAL;
+    auto kern = cpr_stage_kernel<T, P, EQ, DIV, FLUX, TX, TY, stage_delta<T>()>;
     // the prefetching instantiation only where the compensated FP32 stages
     // run on large states: Euler, LP divergence, Rusanov flux
     constexpr bool HAS_PF = sizeof(T) == 4 && EQ == EQ_EULER && DIV == DIV_LP && FLUX == FLUX_RUSANOV;
-    auto kern_pf = cpr_stage_kernel<T, P, EQ, DIV, FLUX, kTileX, kTileY, stage_delta<T>(), HAS_PF>;
+    auto kern_pf = cpr_stage_kernel<T, P, EQ, DIV, FLUX, TX, TY, stage_delta<T>(), HAS_PF>;
     // and the one for grids of at most two CTAs per SM: FP32 Euler, every
     // divergence and flux
     constexpr bool HAS_WIDE = sizeof(T) == 4 && EQ == EQ_EULER;
-    auto kern_w = cpr_stage_kernel<T, P, EQ, DIV, FLUX, kTileX, kTileY, stage_delta<T>(), false, HAS_WIDE>;
+    auto kern_w = cpr_stage_kernel<T, P, EQ, DIV, FLUX, TX, TY, stage_delta<T>(), false, HAS_WIDE>;
+    // CTAs per SM the wide instantiation is compiled for: the grid fits the
+    // device at once up to that many per SM
+    constexpr int WIDE_PER_SM = stage_min_blocks<T, N, true, TX * TY>();
     if (prep) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess && HAS_PF)
@@ -35,7 +39,7 @@ static cudaError_t stage_one(const LaunchCfg& c, const StageArgs<T>& A, int ctas
         return e;
     }
     if (HAS_PF && A.pf_lo) kern_pf<<<ctas, NT, smem, s>>>(A);
-    else if (HAS_WIDE && c.sms > 0 && ctas <= 2 * c.sms) kern_w<<<ctas, NT, smem, s>>>(A);
+    else if (HAS_WIDE && c.sms > 0 && ctas <= WIDE_PER_SM * c.sms) kern_w<<<ctas, NT, smem, s>>>(A);
     else kern<<<ctas, NT, smem, s>>>(A);
     return cudaGetLastError();
 }
@@ -73,7 +77,7 @@ static StageArgs<T> make_stage_args(const LaunchCfg& c, int mode, const StagePtr
     A.ny = c.ny;
     A.bcx = c.bcx;
     A.bcy = c.bcy;
-    A.tiles_x = (c.nx + kTileX - 1) / kTileX;
+    A.tiles_x = (c.nx + stage_tile_x(c.p) - 1) / stage_tile_x(c.p);
     A.mode = mode;
     A.do_avg = b.avg != nullptr;
     A.do_wave = do_wave;

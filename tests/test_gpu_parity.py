@@ -115,8 +115,9 @@ def test_residual_parity_fp32(case):
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
 def test_fp32_residual_on_both_sides_of_the_two_ctas_per_sm_grid(p):
     """The FP32 Euler / LP / Rusanov stage kernel has an instantiation for
-    grids of at most two 8x8-element CTAs per SM (more registers) and one for
-    larger grids: a grid just past that bound and a small one both match the
+    grids that fit the device at once (at most two 8x8-element CTAs per SM,
+    four 8x4-element ones for p = 4; more registers) and one for larger
+    grids: a grid just past that bound and a small one both match the
     oracle."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     ty = 2 * sms // 24 + 2
