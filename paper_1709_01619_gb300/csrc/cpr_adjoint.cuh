@@ -68,8 +68,13 @@ struct VjpLayout {
     __device__ static int yq(int v, int ty, int tx, int k) { return ((v * TY + ty) * TX + tx) * N + k; }
 };
 
+// Resident CTAs per SM the register budget is sized for (0: no bound).
+#ifndef CPR_VJP_MINB
+#define CPR_VJP_MINB 0
+#endif
+
 template <class T, int P, int EQ, int FLUX, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY * (P + 1)) cpr_residual_vjp_kernel(const VjpArgs<T> A)
+__global__ void __launch_bounds__(TX * TY * (P + 1), CPR_VJP_MINB) cpr_residual_vjp_kernel(const VjpArgs<T> A)
 {
     constexpr int N = P + 1, NN = N * N, V = NVars<EQ>::value;
     constexpr int NT = TX * TY * N;
