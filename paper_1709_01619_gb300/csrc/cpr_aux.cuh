@@ -20,6 +20,8 @@ struct AuxArgs {
     double* partials; // norms: per-CTA FP64 partial results
     long long ne, npts;
     int nx, ny, bcx, bcy;
+    unsigned int nx_magic;  // e / nx = div_invariant(e, nx, nx_magic, nx_shift) for e < 2^32
+    int nx_shift;
     int do_wave;
     int check_done;   // limiter inside a step: do nothing once t_end is reached
     T hx, hy, tvb_M, lim_eps;
@@ -28,6 +30,25 @@ struct AuxArgs {
     Tab<double> tab64;  // FP64 weights for the norms
     double gamma64, ax64, ay64;
 };
+
+// Unsigned division by an invariant divisor d (Granlund & Montgomery,
+// "Division by Invariant Integers using Multiplication", 1994): with
+// l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1, n / d is
+// (t + ((n - t) >> 1)) >> (l - 1), t the high word of m n, for every 32-bit
+// n; d = 1 is n itself.  div_magic runs on the host.
+inline void div_magic(unsigned int d, unsigned int* m, int* l)
+{
+    int s = 0;
+    while (s < 32 && (1ull << s) < d) ++s;
+    *l = s;
+    *m = (unsigned int)((((1ull << 32) * ((1ull << s) - d)) / d + 1) & 0xffffffffull);
+}
+__device__ __forceinline__ unsigned int div_invariant(unsigned int n, unsigned int d, unsigned int m, int l)
+{
+    if (d == 1u) return n;
+    const unsigned int t = __umulhi(m, n);
+    return (t + ((n - t) >> 1)) >> (l - 1);
+}
 
 // Element average with the same operation order as the stage kernel: row sums
 // with the per-row weights, then the sum over rows.
@@ -190,13 +211,14 @@ __global__ void __launch_bounds__(LimShape<T, P, EQ>::NT) cpr_limit_kernel(const
     // own and neighbour averages first: their loads overlap the staging of
     // the element values below
     const long long e = e0 + min(le, max(cnt - 1, 0));
-    // element (i, j): 32-bit division when the grid allows it (a 64-bit
-    // division by a runtime value costs over a hundred instructions)
+    // element (i, j): a multiplication by the divisor's magic number while
+    // the element index fits 32 bits (a division by a runtime value costs
+    // tens of instructions, a 64-bit one over a hundred)
     int i, j;
-    if (A.ne <= 0x7fffffffll) {
-        const int ei = (int)e;
-        j = ei / A.nx;
-        i = ei - j * A.nx;
+    if (A.ne <= 0xffffffffll) {
+        const unsigned int eu = (unsigned int)e;
+        j = (int)div_invariant(eu, (unsigned int)A.nx, A.nx_magic, A.nx_shift);
+        i = (int)(eu - (unsigned int)j * (unsigned int)A.nx);
     } else {
         j = (int)(e / A.nx);
         i = (int)(e - (long long)j * A.nx);
@@ -261,8 +283,10 @@ __global__ void __launch_bounds__(LimShape<T, P, EQ>::NT) cpr_limit_kernel(const
     __syncthreads();
     const int marked = le < cnt ? s_mark[le] : 0;
     if (marked) {
-        const T sx = minmod2((aR - qk) / A.hx, (qk - aL) / A.hx);
-        const T sy = minmod2((aT - qk) / A.hy, (qk - aB) / A.hy);
+        // mm(D+ / h, D- / h) = mm(D+, D-) / h bit for bit (division by a
+        // positive h keeps the order and signs of the rounded quotients)
+        const T sx = minmod2(aR - qk, qk - aL) / A.hx;
+        const T sy = minmod2(aT - qk, qk - aB) / A.hy;
         T* dst = A.q + v * A.npts + e * NN;
 #pragma unroll
         for (int b = 0; b < N; ++b)

@@ -25,6 +25,7 @@ static AuxArgs<T> make_aux(const LaunchCfg& c)
     A.npts = c.npts;
     A.nx = c.nx;
     A.ny = c.ny;
+    div_magic((unsigned int)c.nx, &A.nx_magic, &A.nx_shift);
     A.bcx = c.bcx;
     A.bcy = c.bcy;
     A.do_wave = 0;
