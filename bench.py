@@ -408,11 +408,13 @@ def batch_headline(args, world, local, peak):
         hout = [torch.empty_like(h).pin_memory() for h in hin]
         b.set_time(0.0, 0)
         b.step_host(hin, hout, BATCH_STEPS)
+        clocks_e2e = ClockSampler(local)
         t0 = time.perf_counter()
         for _ in range(args.steps):
             b.set_time(0.0, 0)
             b.step_host(hin, hout, BATCH_STEPS)
         e2e_s = time.perf_counter() - t0
+        clk_e2e = clocks_e2e.stop()
         e2e_equal = all(torch.equal(h, q.cpu()) for h, q in zip(hout, qs))
     ms_max = max_over_ranks(ms, world)
     updates = dof * 3 * BATCH_STEPS * args.steps
@@ -424,7 +426,8 @@ def batch_headline(args, world, local, peak):
     state_bytes = dof * 16
     kernels_per_step = 3 * (len(cfgs) if per_inst else ngroups)
     out.update(
-        value=value, ms=ms, ms_max=ms_max, dof=dof, clocks=clk, finite=finite, steps_done=steps_done,
+        value=value, ms=ms, ms_max=ms_max, dof=dof, clocks=clk, clocks_e2e=clk_e2e, finite=finite,
+        steps_done=steps_done,
         t_min=min(t_reached), t_max=max(t_reached), e2e=e2e, e2e_equal=e2e_equal, state_bytes=state_bytes,
         tuned=[{"p": p, "family": f, "grid": g} for p, f, g in choices], per_instance=per_inst,
         roofline={"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -955,7 +958,7 @@ def run_cpr(args, world, rank, local):
         "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
     }
     detail = {"headline": {k: head[k] for k in ("tuned", "per_instance", "steps_done", "t_min", "t_max",
-                                                "finite", "e2e_equal")}}
+                                                "finite", "e2e_equal", "clocks_e2e")}}
     if args.quick:
         if rank == 0:
             print(json.dumps(compact(line)), flush=True)
