@@ -56,9 +56,9 @@ struct VjpLayout {
     static constexpr int YT = V * (TY + 1) * TX * N;
     static constexpr int YH = V * TX * N;
     static constexpr int YQ = V * TY * TX * N;
-    // q, rbar and the column accumulator; edge states and edge cotangents of
-    // both directions; face results
-    static constexpr int TOTAL = 3 * SQ + 2 * (XR + XH + YT + YH) + XQ + YQ;
+    // q and rbar (the column accumulator later reuses the tile of q); edge
+    // states and edge cotangents of both directions; face results
+    static constexpr int TOTAL = 2 * SQ + 2 * (XR + XH + YT + YH) + XQ + YQ;
     __device__ static int sq(int v, int el, int pt) { return (v * E + el) * ES + pt; }
     __device__ static int xr(int v, int ty, int f, int k) { return ((v * TY + ty) * (TX + 1) + f) * N + k; }
     __device__ static int xh(int v, int ty, int k) { return (v * TY + ty) * N + k; }
@@ -68,13 +68,20 @@ struct VjpLayout {
     __device__ static int yq(int v, int ty, int tx, int k) { return ((v * TY + ty) * TX + tx) * N + k; }
 };
 
-// Resident CTAs per SM the register budget is sized for (0: no bound).
-#ifndef CPR_VJP_MINB
-#define CPR_VJP_MINB 0
-#endif
+// Resident CTAs per SM the register budget is sized for (0: no bound): in
+// FP32, for tiles of 32 elements, as many as the shared memory holds
+// (p = 2: 8, p = 3: 6 with 16 bytes of spills, p = 4: 4; unbounded, the
+// registers allowed 7, 5 and 3; 1024^2 p = 3: 0.364 -> 0.351 ms per
+// launch), scaled for other tile sizes; FP64 unbounded.
+template <class T, int P, int ELEMS>
+constexpr int vjp_min_blocks()
+{
+    return sizeof(T) == 8 ? 0 : (P == 2 ? 8 : (P == 3 ? 6 : (P == 4 ? 4 : 0))) * 32 / ELEMS;
+}
 
 template <class T, int P, int EQ, int FLUX, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY * (P + 1), CPR_VJP_MINB) cpr_residual_vjp_kernel(const VjpArgs<T> A)
+__global__ void __launch_bounds__(TX * TY * (P + 1), (vjp_min_blocks<T, P, TX * TY>()))
+cpr_residual_vjp_kernel(const VjpArgs<T> A)
 {
     constexpr int N = P + 1, NN = N * N, V = NVars<EQ>::value;
     constexpr int NT = TX * TY * N;
@@ -82,8 +89,11 @@ __global__ void __launch_bounds__(TX * TY * (P + 1), CPR_VJP_MINB) cpr_residual_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sq = reinterpret_cast<T*>(smem_raw);
     T* sr = sq + L::SQ;
-    T* qb = sr + L::SQ;          // column contributions to qbar
-    T* xRq = qb + L::SQ;         // right edge states
+    // column contributions to qbar, over the tile of q: thread (el, k) writes
+    // only the column k of element el that it has read itself, after the
+    // barrier that ends every thread's row reads
+    T* qb = sq;
+    T* xRq = sr + L::SQ;         // right edge states
     T* xRw = xRq + L::XR;        // right-edge flux cotangents  sum xb g_R'
     T* xHq = xRw + L::XR;        // left edge state of the right halo
     T* xHw = xHq + L::XH;        // its left-edge cotangent     sum xb g_L'
@@ -217,6 +227,10 @@ __global__ void __launch_bounds__(TX * TY * (P + 1), CPR_VJP_MINB) cpr_residual_
             xRq[L::xr(v, ty, tx + 1, k)] = eR[v];
             xRw[L::xr(v, ty, tx + 1, k)] = wR[v];
         }
+    }
+    __syncthreads();  // the rows of the tile of q are read: it becomes the column accumulator
+    if (valid) {
+        T q[N][V], xb[N][V], col[N];
         // column k
 #pragma unroll
         for (int b = 0; b < N; ++b)
