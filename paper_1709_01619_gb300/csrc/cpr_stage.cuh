@@ -311,7 +311,7 @@ constexpr bool stage_delta()
 }
 
 // Resident CTAs per SM the register budget is sized for (FP32: as many as the
-// shared memory allows; FP64: one).
+// shared memory allows; FP64: one, two for p = 3).
 #ifndef CPR_STAGE_MINB_FP32
 #define CPR_STAGE_MINB_FP32 4
 #endif
@@ -329,6 +329,12 @@ constexpr bool stage_delta()
 // compiled for two resident CTAs: twice the registers let the compiler keep
 // more loads in flight, which is what bounds a CTA when the SM holds only
 // one or two of them.
+// FP64 p = 3: two resident CTAs (124 registers, no spills; one CTA of 134
+// registers left the 128 x 128 grid two waves deep: 76.2 -> 73.8 ms for 200
+// steps); the other FP64 orders already fit two.
+#ifndef CPR_STAGE_MINB_FP64_N4
+#define CPR_STAGE_MINB_FP64_N4 2
+#endif
 #ifndef CPR_STAGE_MINB_WIDE
 #define CPR_STAGE_MINB_WIDE 2
 #endif
@@ -340,7 +346,7 @@ constexpr int stage_min_blocks()
 {
     static_assert(64 % ELEMS == 0, "tiles of 64 elements or a divisor of it");
     return (64 / ELEMS) *
-           (sizeof(T) == 8 ? 1
+           (sizeof(T) == 8 ? (N == 4 ? CPR_STAGE_MINB_FP64_N4 : 1)
             : WIDE         ? CPR_STAGE_MINB_WIDE
                            : (N == 2 ? CPR_STAGE_MINB_FP32_N2
                                      : (N == 3 ? CPR_STAGE_MINB_FP32_N3
