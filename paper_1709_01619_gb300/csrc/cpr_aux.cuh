@@ -321,8 +321,7 @@ __global__ void __launch_bounds__(LimShape<T, P, EQ>::NT) cpr_limit_kernel(const
                 }
             }
         }
-        m = block_max<T>(m);
-        last_cta_time_update<T>(m, A.ctrl, /*advance=*/true, gridDim.x);
+        block_time_update<T>(m, A.ctrl, /*advance=*/true, gridDim.x);
     }
 }
 
@@ -340,8 +339,7 @@ __global__ void __launch_bounds__(256) cpr_wave_kernel(const AuxArgs<T> A)
         const T s = point_speed<EQ>(qp, A.ph);
         m = s > m ? s : m;
     }
-    m = block_max<T>(m);
-    last_cta_time_update<T>(m, A.ctrl, /*advance=*/false, gridDim.x);
+    block_time_update<T>(m, A.ctrl, /*advance=*/false, gridDim.x);
 }
 
 // FP64 norms, pass 1: each CTA reduces a contiguous element range in a fixed

@@ -169,8 +169,7 @@ __global__ void __launch_bounds__(kFvTX * kFvTY) cpr_fv_stage_kernel(const Stage
     }
     if (A.do_wave) {
         T m = valid ? point_speed<EQ>(o, A.ph) : T(0);
-        m = block_max<T>(m);
-        last_cta_time_update<T>(m, A.ctrl, /*advance=*/true, gridDim.x);
+        block_time_update<T>(m, A.ctrl, /*advance=*/true, gridDim.x);
     }
 }
 

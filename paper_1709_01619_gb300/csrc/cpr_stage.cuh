@@ -884,18 +884,16 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
     // (only CFL runs need the speed; a run of fixed steps only closes the
     // step; the branch is uniform over the grid)
     if (A.do_wave) {
+        const bool cfl = !(A.ctrl->dt_fixed > 0.0);
         T m = T(0);
-        if (!(A.ctrl->dt_fixed > 0.0)) {
-            if (valid) {
+        if (cfl && valid) {
 #pragma unroll
-                for (int a = 0; a < N; ++a) {
-                    T s = point_speed<EQ>(o[a], A.ph);
-                    m = s > m ? s : m;
-                }
+            for (int a = 0; a < N; ++a) {
+                T s = point_speed<EQ>(o[a], A.ph);
+                m = s > m ? s : m;
             }
-            m = block_max<T>(m);
         }
-        last_cta_time_update<T>(m, A.ctrl, /*advance=*/true, nslots);
+        block_time_update<T>(m, A.ctrl, /*advance=*/true, nslots, cfl);
     }
 }
 
