@@ -572,7 +572,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T>& A, const Tab<T>& 
             for (int tv = tid; active && tv < V * LINES; tv += NT) halo_line(tv % LINES, tv / LINES, V);
         }
     }
-    __syncthreads();
+    // Phase 2 reads only the rows of its own element from the tile copy.  For
+    // even N the column identity is the row identity and a warp holds whole
+    // elements (32 % N == 0), so the rows it reads were written by its own
+    // warp: a warp barrier orders them.  Everything else phase 1 writes
+    // (edge states, halo lines) is read after the next CTA barrier.
+    if constexpr (N % 2 == 0 && 32 % N == 0 && !DELTA) __syncwarp();
+    else __syncthreads();
 
     // ---- phase 2: y-line (column kc of element elc) --------------------------
     // Column identity of the thread.  Odd N: k-major (a warp holds one column
