@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(LimShape<T, P, EQ>::NT) cpr_limit_kernel(const
     constexpr int ES = LimStride<N>::ES;
     __shared__ T sm[V * EB * ES];
     __shared__ int s_mark[EB];
-    __shared__ int s_cnt;
+    static_assert(EB % 32 == 0, "one variable per warp");
     if (A.check_done && A.ctrl->done) return;  // uniform exit
     const long long e0 = (long long)blockIdx.x * EB;
     const int cnt = (int)min((long long)EB, A.ne - e0);
@@ -233,7 +233,6 @@ __global__ void __launch_bounds__(LimShape<T, P, EQ>::NT) cpr_limit_kernel(const
     const T aB = eB >= 0 ? av[eB] : qk, aT = eT >= 0 ? av[eT] : qk;
     load_elements_all<N, V, EB, NT>(A.q, A.npts, e0, cnt, sm);
     if (threadIdx.x < EB) s_mark[threadIdx.x] = 0;
-    if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
     T* mine = &sm[(v * EB + le) * ES];
     if (le < cnt) {
@@ -299,14 +298,16 @@ __global__ void __launch_bounds__(LimShape<T, P, EQ>::NT) cpr_limit_kernel(const
                 dst[b * N + a] = val;
             }
     }
-    if (v == 0 && le < cnt) {
-        A.marks[e] = marked;
-        if (marked) atomicAdd(&s_cnt, 1);  // integer count: order-independent
+    if (v == 0) {
+        // the marks, and their count per warp (a ballot; EB is a multiple of
+        // 32, so v is uniform over a warp) added to the run's integer count
+        if (le < cnt) A.marks[e] = marked;
+        const unsigned int bal = __ballot_sync(0xffffffffu, le < cnt && marked);
+        if ((threadIdx.x & 31) == 0 && bal)
+            atomicAdd(reinterpret_cast<unsigned long long*>(&A.ctrl->marked), (unsigned long long)__popc(bal));
     }
-    __syncthreads();
-    if (threadIdx.x == 0 && s_cnt) atomicAdd(reinterpret_cast<unsigned long long*>(&A.ctrl->marked),
-                                             (unsigned long long)s_cnt);
     if (A.do_wave) {
+        __syncthreads();  // the limited values of the element's other variables
         T m = T(0);
         if (le < cnt) {
 #pragma unroll
