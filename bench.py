@@ -68,13 +68,13 @@ MOVED_ARRAYS_PER_STEP = 10
 # from ncu captures of the stage kernel (profiles/): the 128^2 workload
 # replayed cold (writes stay in L2) and the 1024^2 case.
 NCU_TRAFFIC_128 = 8.429e6
-NCU_TRAFFIC_1024 = 8.573e8
+NCU_TRAFFIC_1024 = 8.575e8
 # The headline batch: DRAM bytes per batch stage (the 64 instances' stage
 # launches of three RK3 steps, replayed one at a time with cold caches,
 # divided by the 9 stages): reads 893.9 MB, the 6 input arrays per RK3 step
-# of the increment form, writes 4.5 MB (the results stay in L2 at the end of
+# of the increment form, writes 4.3 MB (the results stay in L2 at the end of
 # each replayed launch) (profiles/launches_batch64_fp32.md).
-NCU_TRAFFIC_BATCH_STAGE = 8.984e8
+NCU_TRAFFIC_BATCH_STAGE = 8.982e8
 FALLBACK_HBM_GBS = 6800.0
 # FP64 floating-point operations per DOF-stage of the Euler LP stage at
 # p = 3: the method's own count (point fluxes about 25, the two line
