@@ -259,8 +259,13 @@ cpr_status cpr_batch_step(cpr_batch* b, void* const* q_devs, int nsteps, double 
 /* Same as cpr_batch_step for states held in HOST memory: copies every
  * q_in_host[i] (layout of cfgs[i]) to a batch-owned device array (allocated
  * on first use), steps, copies the results to q_out_host[i] (may equal
- * q_in_host[i]) and synchronises.  Pinned host memory gives the fastest
- * copies. */
+ * q_in_host[i]) and synchronises; the results equal cpr_batch_step's bit for
+ * bit.  In the per-instance form (cpr_batch_set_form / cpr_batch_tune), with
+ * nsteps >= 16 and every buffer page-locked (cudaHostAlloc or registered),
+ * each instance's copies run in its own chain of steps, so that they
+ * overlap the steps of other instances; the graphs that do this are bound
+ * to the host buffers and captured again when the buffers change.  Other
+ * calls copy in, step and copy out one after the other. */
 cpr_status cpr_batch_step_host(cpr_batch* b, const void* const* q_in_host, void* const* q_out_host, int nsteps,
                                double dt_fixed, double t_end);
 

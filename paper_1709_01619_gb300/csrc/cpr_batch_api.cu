@@ -58,6 +58,17 @@ struct cpr_batch {
     std::vector<long long> nstate;
     std::vector<void*> Y, Z, lo;
     std::vector<void*> host_state;  // device copies for cpr_batch_step_host (first use)
+    // cpr_batch_step_host in the per-instance form: a head graph whose chain
+    // of instance i starts with the copy of its state in, and a tail graph
+    // whose chain ends with the copy out, so that the copies of some
+    // instances overlap the steps of others; bound to the host buffers (and
+    // the run kind and tail length) they were captured for
+    cudaGraphExec_t gh_head = nullptr, gh_tail = nullptr;
+    std::vector<const void*> gh_in;
+    std::vector<void*> gh_out;
+    int gh_tail_steps = -1;
+    int gh_cfl = -1;
+    std::vector<int> order;  // instances by decreasing state size (copies of the largest first)
     Ctrl* ctrls = nullptr;
     Ctrl* h_ctrls = nullptr;      // pinned
     Ctrl* ctrl_backup = nullptr;  // device, for the autotuner
@@ -202,27 +213,37 @@ cudaError_t ensure_inst_streams(cpr_batch* b)
 // as independent chains: fork from s, one stream per instance, join back.
 // timing != 0: only stages 1 and 2 with swap 0 (they leave the caller's
 // states, the low parts and the time control untouched), for the autotuner.
+// `steps` RK3 steps of instance i on stream si (the increment form's high
+// part alternating between the caller's array and Y, starting in the
+// caller's); timing: stages 1 and 2 only, as below.
+cudaError_t enqueue_inst_steps(cpr_batch* b, int i, int steps, cudaStream_t si, bool timing)
+{
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < steps && e == cudaSuccess; ++k) {
+        if (timing) {
+            e = inst_stage(b, i, b->use_inc ? cpr::MODE_INC1 : cpr::MODE_SO1, 0, si);
+            if (e == cudaSuccess) e = inst_stage(b, i, b->use_inc ? cpr::MODE_INC2 : cpr::MODE_SO2, 0, si);
+        } else if (b->use_inc) {
+            const int sw = k % 2;
+            e = inst_stage(b, i, cpr::MODE_INC1, sw, si);
+            if (e == cudaSuccess) e = inst_stage(b, i, cpr::MODE_INC2, sw, si);
+            if (e == cudaSuccess) e = inst_stage(b, i, cpr::MODE_INC3, sw, si);
+        } else {
+            e = inst_stage(b, i, cpr::MODE_SO1, 0, si);
+            if (e == cudaSuccess) e = inst_stage(b, i, cpr::MODE_SO2, 0, si);
+            if (e == cudaSuccess) e = inst_stage(b, i, cpr::MODE_SO3, 0, si);
+        }
+    }
+    return e;
+}
+
 cudaError_t enqueue_inst_chains(cpr_batch* b, int steps, cudaStream_t s, bool timing)
 {
     cudaError_t e = cudaEventRecord(b->fork_ev, s);
     for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
         cudaStream_t si = b->ist[i];
         e = cudaStreamWaitEvent(si, b->fork_ev, 0);
-        for (int k = 0; k < steps && e == cudaSuccess; ++k) {
-            if (timing) {
-                e = inst_stage(b, i, b->use_inc ? cpr::MODE_INC1 : cpr::MODE_SO1, 0, si);
-                if (e == cudaSuccess) e = inst_stage(b, i, b->use_inc ? cpr::MODE_INC2 : cpr::MODE_SO2, 0, si);
-            } else if (b->use_inc) {
-                const int sw = k % 2;
-                e = inst_stage(b, i, cpr::MODE_INC1, sw, si);
-                if (e == cudaSuccess) e = inst_stage(b, i, cpr::MODE_INC2, sw, si);
-                if (e == cudaSuccess) e = inst_stage(b, i, cpr::MODE_INC3, sw, si);
-            } else {
-                e = inst_stage(b, i, cpr::MODE_SO1, 0, si);
-                if (e == cudaSuccess) e = inst_stage(b, i, cpr::MODE_SO2, 0, si);
-                if (e == cudaSuccess) e = inst_stage(b, i, cpr::MODE_SO3, 0, si);
-            }
-        }
+        if (e == cudaSuccess) e = enqueue_inst_steps(b, i, steps, si, timing);
         if (e == cudaSuccess) e = cudaEventRecord(b->iev[i], si);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->iev[i], 0);
     }
@@ -269,7 +290,12 @@ void drop_graphs(cpr_batch* b)
     if (b->g1) cudaGraphExecDestroy(b->g1);
     if (b->g2) cudaGraphExecDestroy(b->g2);
     if (b->gK) cudaGraphExecDestroy(b->gK);
-    b->g1 = b->g2 = b->gK = nullptr;
+    if (b->gh_head) cudaGraphExecDestroy(b->gh_head);
+    if (b->gh_tail) cudaGraphExecDestroy(b->gh_tail);
+    b->g1 = b->g2 = b->gK = b->gh_head = b->gh_tail = nullptr;
+    b->gh_in.clear();
+    b->gh_out.clear();
+    b->gh_tail_steps = b->gh_cfl = -1;
     b->graphs_valid = false;
 }
 
@@ -553,10 +579,15 @@ static cpr_status batch_bind(cpr_batch* b, void* const* q)
     return CPR_OK;
 }
 
-static cpr_status batch_prelude(cpr_batch* b, void* const* q, double dt_fixed, double t_end, double* cfl_h_dev)
+// The step size and end time of every instance's control block; then, unless
+// the caller's graphs do it per instance (in_graph), the first CFL step size
+// of every instance and the cleared low parts.
+static cpr_status batch_prelude(cpr_batch* b, void* const* q, double dt_fixed, double t_end, double* cfl_h_dev,
+                                bool in_graph)
 {
     batch_configure_kernel<<<(b->n + 127) / 128, 128, 0, b->stream>>>(b->ctrls, b->n, dt_fixed, t_end, cfl_h_dev);
     BATCH_CUDA(b, cudaGetLastError());
+    if (in_graph) return CPR_OK;
     if (dt_fixed <= 0.0)
         for (int i = 0; i < b->n; ++i)
             BATCH_CUDA(b, b->dtype == CPR_F32 ? cpr::launch_wave<float>(b->lcs[i], q[i], b->stream)
@@ -567,9 +598,12 @@ static cpr_status batch_prelude(cpr_batch* b, void* const* q, double dt_fixed, d
     return CPR_OK;
 }
 
-extern "C" cpr_status cpr_batch_step(cpr_batch* b, void* const* q, int nsteps, double dt_fixed, double t_end)
+// Argument checks, binding and the prelude shared by the device and host
+// entry points; *run is false when there is nothing to step.
+static cpr_status batch_begin(cpr_batch* b, void* const* q, int nsteps, double dt_fixed, double t_end,
+                              bool in_graph, bool* run)
 {
-    if (!b) return CPR_EINVAL;
+    *run = false;
     if (nsteps < 0 || !std::isfinite(dt_fixed) || !std::isfinite(t_end)) {
         b->err = "nsteps must be >= 0, dt_fixed and t_end finite";
         return CPR_EINVAL;
@@ -589,7 +623,17 @@ extern "C" cpr_status cpr_batch_step(cpr_batch* b, void* const* q, int nsteps, d
     for (int i = 0; i < b->n; ++i) cflh[i] = b->cfgs[i].cfl * std::min(b->lcs[i].hx, b->lcs[i].hy);
     double* cflh_dev = reinterpret_cast<double*>(b->ctrl_backup);
     BATCH_CUDA(b, cudaMemcpyAsync(cflh_dev, cflh, sizeof(double) * b->n, cudaMemcpyHostToDevice, b->stream));
-    if ((st = batch_prelude(b, q, dt_fixed, t_end, cflh_dev)) != CPR_OK) return st;
+    if ((st = batch_prelude(b, q, dt_fixed, t_end, cflh_dev, in_graph)) != CPR_OK) return st;
+    *run = true;
+    return CPR_OK;
+}
+
+extern "C" cpr_status cpr_batch_step(cpr_batch* b, void* const* q, int nsteps, double dt_fixed, double t_end)
+{
+    if (!b) return CPR_EINVAL;
+    bool run = false;
+    cpr_status st = batch_begin(b, q, nsteps, dt_fixed, t_end, false, &run);
+    if (st != CPR_OK || !run) return st;
     BATCH_CUDA(b, ensure_batch_graphs(b));
     for (int k = 0; k < nsteps / kBatchStepsPerGraph; ++k) BATCH_CUDA(b, cudaGraphLaunch(b->gK, b->stream));
     const int rest = nsteps % kBatchStepsPerGraph;
@@ -605,6 +649,76 @@ extern "C" cpr_status cpr_batch_step(cpr_batch* b, void* const* q, int nsteps, d
         for (int k = 0; k < rest; ++k) BATCH_CUDA(b, cudaGraphLaunch(b->g1, b->stream));
     }
     return CPR_OK;
+}
+
+// Head (head = true) or tail graph of the host entry point in the
+// per-instance form: per instance, on its own stream, largest first, the
+// copy of its state in, its first CFL step size (cfl) and cleared low part,
+// then `steps` steps (head); or `steps` steps, the copy back of a state left
+// in Y and the copy of the state out (tail).
+static cudaError_t capture_host_graph(cpr_batch* b, bool head, const void* const* q_in, void* const* q_out,
+                                      int steps, bool cfl, cudaGraphExec_t* exec)
+{
+    const size_t esize = b->dtype == CPR_F32 ? 4 : 8;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t ee = cudaEventRecord(b->fork_ev, b->cap);
+    for (int r = 0; r < b->n && ee == cudaSuccess; ++r) {
+        const int i = b->order[r];
+        cudaStream_t si = b->ist[i];
+        const size_t bytes = (size_t)b->nstate[i] * esize;
+        ee = cudaStreamWaitEvent(si, b->fork_ev, 0);
+        if (head) {
+            if (ee == cudaSuccess)
+                ee = cudaMemcpyAsync(b->host_state[i], q_in[i], bytes, cudaMemcpyHostToDevice, si);
+            if (ee == cudaSuccess && cfl)
+                ee = b->dtype == CPR_F32 ? cpr::launch_wave<float>(b->lcs[i], b->host_state[i], si)
+                                         : cpr::launch_wave<double>(b->lcs[i], b->host_state[i], si);
+            if (ee == cudaSuccess && b->use_inc) ee = cudaMemsetAsync(b->lo[i], 0, (size_t)b->nstate[i] * 4, si);
+        }
+        if (ee == cudaSuccess) ee = enqueue_inst_steps(b, i, steps, si, false);
+        if (!head) {
+            if (ee == cudaSuccess && b->use_inc) {
+                // this instance's entry in its order group's table
+                for (Group& gr : b->groups)
+                    for (size_t m = 0; m < gr.members.size(); ++m)
+                        if (gr.members[m] == i) {
+                            batch_parity_copy_kernel<float><<<dim3(64, 1), 256, 0, si>>>(
+                                static_cast<const BatchInst<float>*>(gr.d_inst[0]) + m, b->V);
+                            ee = cudaGetLastError();
+                        }
+            }
+            if (ee == cudaSuccess)
+                ee = cudaMemcpyAsync(q_out[i], b->host_state[i], bytes, cudaMemcpyDeviceToHost, si);
+        }
+        if (ee == cudaSuccess) ee = cudaEventRecord(b->iev[i], si);
+        if (ee == cudaSuccess) ee = cudaStreamWaitEvent(b->cap, b->iev[i], 0);
+    }
+    e = cudaStreamEndCapture(b->cap, &g);
+    if (ee != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return ee;
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
+// Every host buffer page-locked (a copy from pageable memory cannot be
+// captured in a graph).
+static bool all_pinned(int n, const void* const* a)
+{
+    for (int i = 0; i < n; ++i) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, a[i]) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return false;
+        }
+        if (at.type != cudaMemoryTypeHost) return false;
+    }
+    return true;
 }
 
 extern "C" cpr_status cpr_batch_step_host(cpr_batch* b, const void* const* q_in, void* const* q_out, int nsteps,
@@ -633,14 +747,64 @@ extern "C" cpr_status cpr_batch_step_host(cpr_batch* b, const void* const* q_in,
             }
         }
     }
-    for (int i = 0; i < b->n; ++i)
-        BATCH_CUDA(b, cudaMemcpyAsync(b->host_state[i], q_in[i], (size_t)b->nstate[i] * esize,
-                                      cudaMemcpyHostToDevice, b->stream));
-    const cpr_status st = cpr_batch_step(b, b->host_state.data(), nsteps, dt_fixed, t_end);
-    if (st != CPR_OK) return st;
-    for (int i = 0; i < b->n; ++i)
-        BATCH_CUDA(b, cudaMemcpyAsync(q_out[i], b->host_state[i], (size_t)b->nstate[i] * esize,
-                                      cudaMemcpyDeviceToHost, b->stream));
+    const int K = kBatchStepsPerGraph;
+    const bool overlap = b->per_inst && nsteps >= 2 * K && all_pinned(b->n, q_in) &&
+                         all_pinned(b->n, const_cast<const void* const*>(q_out));
+    if (!overlap) {
+        // grouped form, short runs or pageable buffers: copies in, the steps,
+        // copies out, one after the other
+        for (int i = 0; i < b->n; ++i)
+            BATCH_CUDA(b, cudaMemcpyAsync(b->host_state[i], q_in[i], (size_t)b->nstate[i] * esize,
+                                          cudaMemcpyHostToDevice, b->stream));
+        const cpr_status st = cpr_batch_step(b, b->host_state.data(), nsteps, dt_fixed, t_end);
+        if (st != CPR_OK) return st;
+        for (int i = 0; i < b->n; ++i)
+            BATCH_CUDA(b, cudaMemcpyAsync(q_out[i], b->host_state[i], (size_t)b->nstate[i] * esize,
+                                          cudaMemcpyDeviceToHost, b->stream));
+        BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+        return CPR_OK;
+    }
+    // Per-instance form: the head graph copies each instance in and runs its
+    // first K steps on its own stream (largest instances first), so later
+    // copies overlap earlier instances' steps; the middle runs the usual
+    // K-step graphs; the tail graph runs each instance's last K..2K-1 steps
+    // and copies it out, overlapping the copies of the instances that finish
+    // first with the steps of the others.  The same kernels in the same
+    // order per instance: the results equal the device entry point's.
+    bool run = false;
+    cpr_status st = batch_begin(b, b->host_state.data(), nsteps, dt_fixed, t_end, true, &run);
+    if (st != CPR_OK || !run) return st;
+    BATCH_CUDA(b, ensure_inst_streams(b));
+    if ((int)b->order.size() != b->n) {
+        b->order.resize(b->n);
+        for (int i = 0; i < b->n; ++i) b->order[i] = i;
+        std::stable_sort(b->order.begin(), b->order.end(),
+                         [b](int x, int y) { return b->nstate[x] > b->nstate[y]; });
+    }
+    BATCH_CUDA(b, ensure_batch_graphs(b));
+    const int tail = K + nsteps % K, mid = (nsteps - K - tail) / K;
+    const int cfl = dt_fixed <= 0.0 ? 1 : 0;
+    const bool same_in = (int)b->gh_in.size() == b->n && std::equal(b->gh_in.begin(), b->gh_in.end(), q_in);
+    const bool same_out = (int)b->gh_out.size() == b->n && std::equal(b->gh_out.begin(), b->gh_out.end(), q_out);
+    if (!b->gh_head || !same_in || b->gh_cfl != cfl) {
+        if (b->gh_head) cudaGraphExecDestroy(b->gh_head);
+        b->gh_head = nullptr;
+        b->gh_in.clear();
+        BATCH_CUDA(b, capture_host_graph(b, true, q_in, q_out, K, cfl != 0, &b->gh_head));
+        b->gh_in.assign(q_in, q_in + b->n);
+        b->gh_cfl = cfl;
+    }
+    if (!b->gh_tail || !same_out || b->gh_tail_steps != tail) {
+        if (b->gh_tail) cudaGraphExecDestroy(b->gh_tail);
+        b->gh_tail = nullptr;
+        b->gh_out.clear();
+        BATCH_CUDA(b, capture_host_graph(b, false, q_in, q_out, tail, cfl != 0, &b->gh_tail));
+        b->gh_out.assign(q_out, q_out + b->n);
+        b->gh_tail_steps = tail;
+    }
+    BATCH_CUDA(b, cudaGraphLaunch(b->gh_head, b->stream));
+    for (int k = 0; k < mid; ++k) BATCH_CUDA(b, cudaGraphLaunch(b->gK, b->stream));
+    BATCH_CUDA(b, cudaGraphLaunch(b->gh_tail, b->stream));
     BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
     return CPR_OK;
 }

@@ -163,3 +163,44 @@ def test_batch_step_host_matches_device_step():
         assert all(b.get_time(i)[1] == 5 for i in range(len(cs)))
     for d, h in zip(qd, hout):
         assert torch.equal(d.cpu(), h)
+
+
+@pytest.mark.parametrize("dtype", [nat.F32, nat.F64])
+@pytest.mark.parametrize("nsteps,dt,t_end", [(21, 0.0, 0.0), (37, 0.0, 0.0), (16, 0.004, 0.0), (40, 0.0, 0.05)])
+def test_batch_step_host_overlapped_matches_device_step(dtype, nsteps, dt, t_end):
+    """The host entry point in the per-instance form with page-locked
+    buffers (copies in the chains of a head and a tail graph, overlapping
+    other instances' steps) against the device entry point: the same
+    states bit for bit, step counts and times, for CFL and fixed steps, an
+    end time that stops instances early, odd and even tails, and two calls
+    in a row (the second one reusing the graphs bound to the buffers); then
+    pageable buffers, which take the plain path, the same again."""
+    cs = cfgs(dtype)
+    q0s = [initial(c, s[3]) for c, s in zip(cs, SHAPES)]
+    with nat.Batch(cs) as b:
+        b.set_form(True)
+        qd = [q.clone() for q in q0s]
+        b.step(qd, nsteps, dt, t_end)
+        td = [b.get_time(i) for i in range(len(cs))]
+        b.set_time(0.0, 0)
+        b.step(qd, nsteps, dt, t_end)
+        td2 = [b.get_time(i) for i in range(len(cs))]
+    with nat.Batch(cs) as b:
+        b.set_form(True)
+        hin = [q.cpu().pin_memory() for q in q0s]
+        hout = [torch.empty_like(h).pin_memory() for h in hin]
+        b.step_host(hin, hout, nsteps, dt, t_end)
+        assert [b.get_time(i) for i in range(len(cs))] == td
+        b.set_time(0.0, 0)
+        b.step_host(hout, hout, nsteps, dt, t_end)
+        assert [b.get_time(i) for i in range(len(cs))] == td2
+        for d, h in zip(qd, hout):
+            assert torch.equal(d.cpu(), h)
+        pin = [q.cpu() for q in q0s]
+        pout = [torch.empty_like(h) for h in pin]
+        b.set_time(0.0, 0)
+        b.step_host(pin, pout, nsteps, dt, t_end)
+        b.set_time(0.0, 0)
+        b.step_host(pout, pout, nsteps, dt, t_end)
+        for d, h in zip(qd, pout):
+            assert torch.equal(d.cpu(), h)
