@@ -69,6 +69,12 @@ struct cpr_batch {
     int gh_tail_steps = -1;
     int gh_cfl = -1;
     std::vector<int> order;  // instances by decreasing state size (copies of the largest first)
+    // cpr_batch_step in the per-instance form: the same head and tail graphs
+    // without the copies (the first CFL step sizes and cleared low parts of
+    // every instance in its own chain instead of one stream)
+    cudaGraphExec_t gd_head = nullptr, gd_tail = nullptr;
+    int gd_tail_steps = -1;
+    int gd_cfl = -1;
     Ctrl* ctrls = nullptr;
     Ctrl* h_ctrls = nullptr;      // pinned
     Ctrl* ctrl_backup = nullptr;  // device, for the autotuner
@@ -292,7 +298,10 @@ void drop_graphs(cpr_batch* b)
     if (b->gK) cudaGraphExecDestroy(b->gK);
     if (b->gh_head) cudaGraphExecDestroy(b->gh_head);
     if (b->gh_tail) cudaGraphExecDestroy(b->gh_tail);
-    b->g1 = b->g2 = b->gK = b->gh_head = b->gh_tail = nullptr;
+    if (b->gd_head) cudaGraphExecDestroy(b->gd_head);
+    if (b->gd_tail) cudaGraphExecDestroy(b->gd_tail);
+    b->g1 = b->g2 = b->gK = b->gh_head = b->gh_tail = b->gd_head = b->gd_tail = nullptr;
+    b->gd_tail_steps = b->gd_cfl = -1;
     b->gh_in.clear();
     b->gh_out.clear();
     b->gh_tail_steps = b->gh_cfl = -1;
@@ -628,34 +637,12 @@ static cpr_status batch_begin(cpr_batch* b, void* const* q, int nsteps, double d
     return CPR_OK;
 }
 
-extern "C" cpr_status cpr_batch_step(cpr_batch* b, void* const* q, int nsteps, double dt_fixed, double t_end)
-{
-    if (!b) return CPR_EINVAL;
-    bool run = false;
-    cpr_status st = batch_begin(b, q, nsteps, dt_fixed, t_end, false, &run);
-    if (st != CPR_OK || !run) return st;
-    BATCH_CUDA(b, ensure_batch_graphs(b));
-    for (int k = 0; k < nsteps / kBatchStepsPerGraph; ++k) BATCH_CUDA(b, cudaGraphLaunch(b->gK, b->stream));
-    const int rest = nsteps % kBatchStepsPerGraph;
-    if (b->use_inc) {
-        for (int k = 0; k < rest / 2; ++k) BATCH_CUDA(b, cudaGraphLaunch(b->g2, b->stream));
-        if (rest % 2) BATCH_CUDA(b, cudaGraphLaunch(b->g1, b->stream));
-        for (Group& g : b->groups) {
-            batch_parity_copy_kernel<float><<<dim3(64, (unsigned)g.members.size()), 256, 0, b->stream>>>(
-                static_cast<const BatchInst<float>*>(g.d_inst[0]), b->V);
-            BATCH_CUDA(b, cudaGetLastError());
-        }
-    } else {
-        for (int k = 0; k < rest; ++k) BATCH_CUDA(b, cudaGraphLaunch(b->g1, b->stream));
-    }
-    return CPR_OK;
-}
-
-// Head (head = true) or tail graph of the host entry point in the
-// per-instance form: per instance, on its own stream, largest first, the
-// copy of its state in, its first CFL step size (cfl) and cleared low part,
+// Head (head = true) or tail graph of a run in the per-instance form: per
+// instance, on its own stream, largest first, the copy of its state in (host
+// entry point: q_in), its first CFL step size (cfl) and cleared low part,
 // then `steps` steps (head); or `steps` steps, the copy back of a state left
-// in Y and the copy of the state out (tail).
+// in Y and the copy of the state out (q_out) (tail).  The instance states are
+// the bound arrays (x_cached).
 static cudaError_t capture_host_graph(cpr_batch* b, bool head, const void* const* q_in, void* const* q_out,
                                       int steps, bool cfl, cudaGraphExec_t* exec)
 {
@@ -669,12 +656,13 @@ static cudaError_t capture_host_graph(cpr_batch* b, bool head, const void* const
         cudaStream_t si = b->ist[i];
         const size_t bytes = (size_t)b->nstate[i] * esize;
         ee = cudaStreamWaitEvent(si, b->fork_ev, 0);
+        void* X = const_cast<void*>(b->x_cached[i]);
         if (head) {
-            if (ee == cudaSuccess)
-                ee = cudaMemcpyAsync(b->host_state[i], q_in[i], bytes, cudaMemcpyHostToDevice, si);
+            if (ee == cudaSuccess && q_in)
+                ee = cudaMemcpyAsync(X, q_in[i], bytes, cudaMemcpyHostToDevice, si);
             if (ee == cudaSuccess && cfl)
-                ee = b->dtype == CPR_F32 ? cpr::launch_wave<float>(b->lcs[i], b->host_state[i], si)
-                                         : cpr::launch_wave<double>(b->lcs[i], b->host_state[i], si);
+                ee = b->dtype == CPR_F32 ? cpr::launch_wave<float>(b->lcs[i], X, si)
+                                         : cpr::launch_wave<double>(b->lcs[i], X, si);
             if (ee == cudaSuccess && b->use_inc) ee = cudaMemsetAsync(b->lo[i], 0, (size_t)b->nstate[i] * 4, si);
         }
         if (ee == cudaSuccess) ee = enqueue_inst_steps(b, i, steps, si, false);
@@ -689,8 +677,8 @@ static cudaError_t capture_host_graph(cpr_batch* b, bool head, const void* const
                             ee = cudaGetLastError();
                         }
             }
-            if (ee == cudaSuccess)
-                ee = cudaMemcpyAsync(q_out[i], b->host_state[i], bytes, cudaMemcpyDeviceToHost, si);
+            if (ee == cudaSuccess && q_out)
+                ee = cudaMemcpyAsync(q_out[i], X, bytes, cudaMemcpyDeviceToHost, si);
         }
         if (ee == cudaSuccess) ee = cudaEventRecord(b->iev[i], si);
         if (ee == cudaSuccess) ee = cudaStreamWaitEvent(b->cap, b->iev[i], 0);
@@ -719,6 +707,93 @@ static bool all_pinned(int n, const void* const* a)
         if (at.type != cudaMemoryTypeHost) return false;
     }
     return true;
+}
+
+// A run of nsteps >= 2K steps in the per-instance form: the head graph (K
+// steps), K-step graphs, the tail graph (K..2K-1 steps); q_in / q_out: the
+// host buffers of the host entry point (null: the device one).
+static cpr_status run_chains(cpr_batch* b, int nsteps, double dt_fixed, const void* const* q_in, void* const* q_out)
+{
+    const int K = kBatchStepsPerGraph;
+    BATCH_CUDA(b, ensure_inst_streams(b));
+    if ((int)b->order.size() != b->n) {
+        b->order.resize(b->n);
+        for (int i = 0; i < b->n; ++i) b->order[i] = i;
+        std::stable_sort(b->order.begin(), b->order.end(),
+                         [b](int x, int y) { return b->nstate[x] > b->nstate[y]; });
+    }
+    BATCH_CUDA(b, ensure_batch_graphs(b));
+    const int tail = K + nsteps % K, mid = (nsteps - K - tail) / K;
+    const int cfl = dt_fixed <= 0.0 ? 1 : 0;
+    cudaGraphExec_t* head = &b->gd_head;
+    cudaGraphExec_t* tailg = &b->gd_tail;
+    if (q_in) {
+        head = &b->gh_head;
+        tailg = &b->gh_tail;
+        const bool same_in = (int)b->gh_in.size() == b->n && std::equal(b->gh_in.begin(), b->gh_in.end(), q_in);
+        const bool same_out =
+            (int)b->gh_out.size() == b->n && std::equal(b->gh_out.begin(), b->gh_out.end(), q_out);
+        if (!b->gh_head || !same_in || b->gh_cfl != cfl) {
+            if (b->gh_head) cudaGraphExecDestroy(b->gh_head);
+            b->gh_head = nullptr;
+            b->gh_in.clear();
+            BATCH_CUDA(b, capture_host_graph(b, true, q_in, q_out, K, cfl != 0, &b->gh_head));
+            b->gh_in.assign(q_in, q_in + b->n);
+            b->gh_cfl = cfl;
+        }
+        if (!b->gh_tail || !same_out || b->gh_tail_steps != tail) {
+            if (b->gh_tail) cudaGraphExecDestroy(b->gh_tail);
+            b->gh_tail = nullptr;
+            b->gh_out.clear();
+            BATCH_CUDA(b, capture_host_graph(b, false, q_in, q_out, tail, cfl != 0, &b->gh_tail));
+            b->gh_out.assign(q_out, q_out + b->n);
+            b->gh_tail_steps = tail;
+        }
+    } else {
+        if (!b->gd_head || b->gd_cfl != cfl) {
+            if (b->gd_head) cudaGraphExecDestroy(b->gd_head);
+            b->gd_head = nullptr;
+            BATCH_CUDA(b, capture_host_graph(b, true, nullptr, nullptr, K, cfl != 0, &b->gd_head));
+            b->gd_cfl = cfl;
+        }
+        if (!b->gd_tail || b->gd_tail_steps != tail) {
+            if (b->gd_tail) cudaGraphExecDestroy(b->gd_tail);
+            b->gd_tail = nullptr;
+            BATCH_CUDA(b, capture_host_graph(b, false, nullptr, nullptr, tail, cfl != 0, &b->gd_tail));
+            b->gd_tail_steps = tail;
+        }
+    }
+    BATCH_CUDA(b, cudaGraphLaunch(*head, b->stream));
+    for (int k = 0; k < mid; ++k) BATCH_CUDA(b, cudaGraphLaunch(b->gK, b->stream));
+    BATCH_CUDA(b, cudaGraphLaunch(*tailg, b->stream));
+    return CPR_OK;
+}
+
+extern "C" cpr_status cpr_batch_step(cpr_batch* b, void* const* q, int nsteps, double dt_fixed, double t_end)
+{
+    if (!b) return CPR_EINVAL;
+    // per-instance form: the first CFL step sizes, the cleared low parts and
+    // the copies back of states left in Y inside the instances' own chains
+    const bool chains = b->per_inst && nsteps >= 2 * kBatchStepsPerGraph;
+    bool run = false;
+    cpr_status st = batch_begin(b, q, nsteps, dt_fixed, t_end, chains, &run);
+    if (st != CPR_OK || !run) return st;
+    if (chains) return run_chains(b, nsteps, dt_fixed, nullptr, nullptr);
+    BATCH_CUDA(b, ensure_batch_graphs(b));
+    for (int k = 0; k < nsteps / kBatchStepsPerGraph; ++k) BATCH_CUDA(b, cudaGraphLaunch(b->gK, b->stream));
+    const int rest = nsteps % kBatchStepsPerGraph;
+    if (b->use_inc) {
+        for (int k = 0; k < rest / 2; ++k) BATCH_CUDA(b, cudaGraphLaunch(b->g2, b->stream));
+        if (rest % 2) BATCH_CUDA(b, cudaGraphLaunch(b->g1, b->stream));
+        for (Group& g : b->groups) {
+            batch_parity_copy_kernel<float><<<dim3(64, (unsigned)g.members.size()), 256, 0, b->stream>>>(
+                static_cast<const BatchInst<float>*>(g.d_inst[0]), b->V);
+            BATCH_CUDA(b, cudaGetLastError());
+        }
+    } else {
+        for (int k = 0; k < rest; ++k) BATCH_CUDA(b, cudaGraphLaunch(b->g1, b->stream));
+    }
+    return CPR_OK;
 }
 
 extern "C" cpr_status cpr_batch_step_host(cpr_batch* b, const void* const* q_in, void* const* q_out, int nsteps,
@@ -774,37 +849,7 @@ extern "C" cpr_status cpr_batch_step_host(cpr_batch* b, const void* const* q_in,
     bool run = false;
     cpr_status st = batch_begin(b, b->host_state.data(), nsteps, dt_fixed, t_end, true, &run);
     if (st != CPR_OK || !run) return st;
-    BATCH_CUDA(b, ensure_inst_streams(b));
-    if ((int)b->order.size() != b->n) {
-        b->order.resize(b->n);
-        for (int i = 0; i < b->n; ++i) b->order[i] = i;
-        std::stable_sort(b->order.begin(), b->order.end(),
-                         [b](int x, int y) { return b->nstate[x] > b->nstate[y]; });
-    }
-    BATCH_CUDA(b, ensure_batch_graphs(b));
-    const int tail = K + nsteps % K, mid = (nsteps - K - tail) / K;
-    const int cfl = dt_fixed <= 0.0 ? 1 : 0;
-    const bool same_in = (int)b->gh_in.size() == b->n && std::equal(b->gh_in.begin(), b->gh_in.end(), q_in);
-    const bool same_out = (int)b->gh_out.size() == b->n && std::equal(b->gh_out.begin(), b->gh_out.end(), q_out);
-    if (!b->gh_head || !same_in || b->gh_cfl != cfl) {
-        if (b->gh_head) cudaGraphExecDestroy(b->gh_head);
-        b->gh_head = nullptr;
-        b->gh_in.clear();
-        BATCH_CUDA(b, capture_host_graph(b, true, q_in, q_out, K, cfl != 0, &b->gh_head));
-        b->gh_in.assign(q_in, q_in + b->n);
-        b->gh_cfl = cfl;
-    }
-    if (!b->gh_tail || !same_out || b->gh_tail_steps != tail) {
-        if (b->gh_tail) cudaGraphExecDestroy(b->gh_tail);
-        b->gh_tail = nullptr;
-        b->gh_out.clear();
-        BATCH_CUDA(b, capture_host_graph(b, false, q_in, q_out, tail, cfl != 0, &b->gh_tail));
-        b->gh_out.assign(q_out, q_out + b->n);
-        b->gh_tail_steps = tail;
-    }
-    BATCH_CUDA(b, cudaGraphLaunch(b->gh_head, b->stream));
-    for (int k = 0; k < mid; ++k) BATCH_CUDA(b, cudaGraphLaunch(b->gK, b->stream));
-    BATCH_CUDA(b, cudaGraphLaunch(b->gh_tail, b->stream));
+    if ((st = run_chains(b, nsteps, dt_fixed, q_in, q_out)) != CPR_OK) return st;
     BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
     return CPR_OK;
 }

@@ -52,7 +52,7 @@ def singles(cs, q0s, nsteps, dt, t_end=0.0):
 
 @pytest.mark.parametrize("per_instance", [False, True])
 @pytest.mark.parametrize("dtype", [nat.F64, nat.F32])
-@pytest.mark.parametrize("nsteps", [1, 2, 5])
+@pytest.mark.parametrize("nsteps", [1, 2, 5, 21])
 def test_batch_matches_single_contexts(dtype, nsteps, per_instance):
     """Grouped form: the same arithmetic as single contexts up to the
     kernels' rounding; per-instance form: the single-problem kernels
@@ -71,6 +71,35 @@ def test_batch_matches_single_contexts(dtype, nsteps, per_instance):
             if per_instance and dtype == nat.F64:
                 assert torch.equal(q, r), i
             assert b.get_time(i)[1] == nsteps
+
+
+@pytest.mark.parametrize("per_instance", [False, True])
+@pytest.mark.parametrize("dtype", [nat.F64, nat.F32])
+def test_batch_cfl_run_matches_single_contexts(dtype, per_instance):
+    """19 CFL steps (in the per-instance form: a head graph whose chains
+    also take each instance's first step size and clear its low part, and a
+    tail graph of 11 steps whose chains copy back a state left in the
+    stage buffer): the states of single contexts (FP64 per-instance bit for
+    bit) and their step counts and times (equal, or within the rounding
+    that the CFL step sizes inherit from the states)."""
+    cs = cfgs(dtype)
+    q0s = [initial(c, s[3]) for c, s in zip(cs, SHAPES)]
+    ref, times = singles(cs, q0s, 19, 0.0)
+    with nat.Batch(cs) as b:
+        b.set_form(per_instance)
+        qs = [q.clone() for q in q0s]
+        b.step(qs, 19, 0.0)
+        for i, (q, r) in enumerate(zip(qs, ref)):
+            assert rel(q, r) <= TOL[dtype], i
+            if per_instance and dtype == nat.F64:
+                assert torch.equal(q, r), i
+            t, n = b.get_time(i)
+            assert n == times[i][1] == 19
+            # the step sizes follow the states' rounding (FP32, grouped form)
+            if per_instance and dtype == nat.F64:
+                assert t == times[i][0]
+            else:
+                assert abs(t - times[i][0]) <= 1e-6 * times[i][0]
 
 
 def test_per_instance_form_follows_new_state_arrays():
