@@ -231,6 +231,23 @@ cpr_status cpr_residual_vjp(cpr_ctx* ctx, const void* q_dev, const void* rbar_de
 cpr_status cpr_step_vjp(cpr_ctx* ctx, const void* q_dev, const void* qbar_out_dev, void* qbar_in_dev,
                         double dt);
 
+/* The two halves of cpr_step_vjp for a reverse sweep over stored steps:
+ * cpr_step_stages runs one SSP-RK3 step of size dt from q_dev in the
+ * Shu-Osher form of Sec. 4, keeping its stage states:
+ *   q1 = q + dt R(q),  q2 = 3/4 q + 1/4 (q1 + dt R(q1)),
+ *   q_next = 1/3 q + 2/3 (q2 + dt R(q2))
+ * (the arithmetic of cpr_step's FP64 path; the context's simulated time is
+ * not advanced); cpr_step_vjp_stages is cpr_step_vjp with those stage states
+ * given instead of recomputed, so a reverse sweep costs the three transposed
+ * residuals per step.  Same conditions as cpr_step_vjp (CPR scheme, LP
+ * divergence, no limiter, dt finite and > 0); q1, q2 and q_next must not
+ * alias q or each other (q_next may be q for cpr_step_stages, which then
+ * overwrites it), the cotangents must not alias any state. */
+cpr_status cpr_step_stages(cpr_ctx* ctx, const void* q_dev, void* q1_dev, void* q2_dev, void* q_next_dev,
+                           double dt);
+cpr_status cpr_step_vjp_stages(cpr_ctx* ctx, const void* q_dev, const void* q1_dev, const void* q2_dev,
+                               const void* qbar_out_dev, void* qbar_in_dev, double dt);
+
 /* ---- batches ------------------------------------------------------------
  * Many independent problems of uneven size and order advanced together (no
  * counterpart in the paper's single-grid runs).  For every SSP-RK3 stage

@@ -34,6 +34,7 @@ EXPORTS = (
     "cpr_init", "cpr_destroy", "cpr_state_elems", "cpr_last_error", "cpr_point_coords",
     "cpr_residual", "cpr_step", "cpr_step_host", "cpr_limit", "cpr_get_marks", "cpr_averages",
     "cpr_norms", "cpr_set_time", "cpr_get_time", "cpr_residual_vjp", "cpr_step_vjp",
+    "cpr_step_stages", "cpr_step_vjp_stages",
     "cpr_step_noalloc", "cpr_batch_init", "cpr_batch_destroy", "cpr_batch_last_error",
     "cpr_batch_step", "cpr_batch_step_host", "cpr_batch_tune", "cpr_batch_set_form", "cpr_batch_get_time",
     "cpr_batch_set_time",
@@ -165,6 +166,10 @@ def load():
             lib.cpr_residual_vjp.argtypes = [P, P, P, P]
             lib.cpr_step_vjp.restype = I
             lib.cpr_step_vjp.argtypes = [P, P, P, P, D]
+            lib.cpr_step_stages.restype = I
+            lib.cpr_step_stages.argtypes = [P, P, P, P, P, D]
+            lib.cpr_step_vjp_stages.restype = I
+            lib.cpr_step_vjp_stages.argtypes = [P, P, P, P, P, P, D]
             lib.cpr_batch_init.restype = I
             lib.cpr_batch_init.argtypes = [ctypes.POINTER(_Config), I, P, ctypes.POINTER(P)]
             lib.cpr_batch_destroy.restype = None
@@ -318,6 +323,24 @@ class Context:
         if qbar_in is None:
             qbar_in = torch.empty_like(q)
         self._check(self.lib.cpr_step_vjp(self.h, _ptr(q), _ptr(qbar_out), _ptr(qbar_in), float(dt)))
+        return qbar_in
+
+    def step_stages(self, q, q1, q2, q_next, dt: float):
+        """One Shu-Osher SSP-RK3 step of size dt from q into q_next, keeping
+        the stage states q1, q2 (cpr_step_stages)."""
+        for t, n in ((q, "q"), (q1, "q1"), (q2, "q2"), (q_next, "q_next")):
+            self._state(t, n)
+        self._check(self.lib.cpr_step_stages(self.h, _ptr(q), _ptr(q1), _ptr(q2), _ptr(q_next), float(dt)))
+        return q_next
+
+    def step_vjp_stages(self, q, q1, q2, qbar_out, dt: float, qbar_in=None):
+        """cpr_step_vjp around the given stage states (cpr_step_vjp_stages)."""
+        for t, n in ((q, "q"), (q1, "q1"), (q2, "q2"), (qbar_out, "qbar_out")):
+            self._state(t, n)
+        if qbar_in is None:
+            qbar_in = torch.empty_like(q)
+        self._check(self.lib.cpr_step_vjp_stages(self.h, _ptr(q), _ptr(q1), _ptr(q2), _ptr(qbar_out),
+                                                 _ptr(qbar_in), float(dt)))
         return qbar_in
 
     def close(self):

@@ -1,12 +1,15 @@
 """Gradients through many SSP-RK3 steps: torch.autograd.Function over the
-hand-written discrete adjoint (cpr_step_vjp), with checkpointed recomputation.
+hand-written discrete adjoint (cpr_step_stages, cpr_step_vjp_stages), with
+checkpointed recomputation.
 
 The forward pass advances q0 by ``nsteps`` fixed steps of size ``dt`` and keeps
 the state every ``every`` steps.  The backward pass walks the segments in
-reverse: it recomputes the states of one segment from its checkpoint and
-applies the transposed step to the cotangent, last step first.  Memory: one
-state per checkpoint plus one segment of states.  Valid for unlimited runs
-with the LP divergence (the adjoint of the limiter is not defined).
+reverse: it recomputes the states of one segment from its checkpoint, with the
+stage states of each step (the Shu-Osher form of Sec. 4), and applies the
+transposed step around them to the cotangent, last step first.  Memory: one
+state per checkpoint plus three states per step of one segment.  Valid for
+unlimited runs with the LP divergence (the adjoint of the limiter is not
+defined).
 """
 from __future__ import annotations
 
@@ -32,24 +35,24 @@ class CPRRollout(torch.autograd.Function):
         solver, nsteps, dt, every = ctx.solver, ctx.nsteps, ctx.dt, ctx.every
         qbar = gout.contiguous().clone()
         tmp = torch.empty_like(qbar)
-        # One work array for the recomputation and one buffer per state of a
-        # segment, allocated once: the context's step graphs are bound to the
-        # state array they step, so a fixed work array keeps them across the
-        # segments (a fresh array per segment would re-capture them).
-        work = torch.empty_like(qbar)
-        bufs = [torch.empty_like(qbar) for _ in range(min(every, nsteps) - 1)]
+        # Buffers for one segment, allocated once per backward pass: its
+        # states after the checkpoint and the two stage states of each of its
+        # steps, so that the reverse sweep applies only the three transposed
+        # residuals per step (cpr_step_vjp_stages) instead of recomputing the
+        # stages.
+        n = min(every, nsteps)
+        xs = [torch.empty_like(qbar) for _ in range(n)]
+        s1 = [torch.empty_like(qbar) for _ in range(n)]
+        s2 = [torch.empty_like(qbar) for _ in range(n)]
         for k in reversed(range(len(ctx.ckpts))):
             start = k * every
-            end = min(start + every, nsteps)
+            m = min(start + every, nsteps) - start
             states = [ctx.ckpts[k]]
-            work.copy_(ctx.ckpts[k])
-            for s in range(start, end - 1):
-                solver.step(work, 1, dt)
-                b = bufs[s - start]
-                b.copy_(work)
-                states.append(b)
-            for s in reversed(range(end - start)):
-                solver.step_vjp(states[s], qbar, dt, tmp)
+            for s in range(m):
+                solver.step_stages(states[s], s1[s], s2[s], xs[s], dt)
+                states.append(xs[s])
+            for s in reversed(range(m)):
+                solver.step_vjp_stages(states[s], s1[s], s2[s], qbar, dt, tmp)
                 qbar, tmp = tmp, qbar
         return qbar, None, None, None, None
 

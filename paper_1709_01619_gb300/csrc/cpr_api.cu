@@ -555,35 +555,86 @@ extern "C" cpr_status cpr_residual_vjp(cpr_ctx* c, const void* q, const void* rb
     return CPR_OK;
 }
 
-// Transpose of one SSP-RK3 step from q with step dt, stages recomputed:
+// Checks shared by the step adjoint entry points.
+static cpr_status step_adjoint_check(cpr_ctx* c, double dt)
+{
+    if (c->cfg.scheme != CPR_SCHEME_CPR) return fail(c, CPR_EINVAL, "no adjoint for the FV schemes");
+    if (c->cfg.flux == CPR_FLUX_ROE) return fail(c, CPR_EINVAL, "no adjoint for the Roe flux");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, CPR_EINVAL, "dt must be finite and > 0");
+    return vjp_check(c);
+}
+
+// Transpose of one SSP-RK3 step from q with step dt around its stage states
+// q1, q2:
 //   b2 = 2/3 (qbar_out + dt J(q2)^T qbar_out)
 //   b1 = 1/4 (b2 + dt J(q1)^T b2)
 //   qbar_in = 1/3 qbar_out + 3/4 b2 + b1 + dt J(q)^T b1
-extern "C" cpr_status cpr_step_vjp(cpr_ctx* c, const void* q, const void* qbar_out, void* qbar_in, double dt)
+static cpr_status step_vjp_chain(cpr_ctx* c, const void* q, const void* q1, const void* q2, const void* qbar_out,
+                                 void* qbar_in, double dt)
 {
-    if (!c) return CPR_EINVAL;
-    if (c->cfg.scheme != CPR_SCHEME_CPR) return fail(c, CPR_EINVAL, "no adjoint for the FV schemes");
-    if (c->cfg.flux == CPR_FLUX_ROE) return fail(c, CPR_EINVAL, "no adjoint for the Roe flux");
-    if (!q || !qbar_out || !qbar_in) return fail(c, CPR_EINVAL, "q_dev, qbar_out_dev and qbar_in_dev must be non-NULL");
-    if (q == qbar_out || q == qbar_in) return fail(c, CPR_EINVAL, "q_dev must not alias the cotangents");
-    if (!aligned(q) || !aligned(qbar_out) || !aligned(qbar_in))
-        return fail(c, CPR_EINVAL, "state arrays must be 16-byte aligned");
-    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, CPR_EINVAL, "dt must be finite and > 0");
-    cpr_status st = vjp_check(c);
-    if (st != CPR_OK) return st;
     const size_t bytes = (size_t)c->nstate * c->esize;
     if (!c->adj1) CPR_CUDA(c, cudaMalloc(&c->adj1, bytes));
     if (!c->adj2) CPR_CUDA(c, cudaMalloc(&c->adj2, bytes));
-    // stage states q1, q2 with this dt (Shu-Osher form, context buffers)
-    ctrl_configure_kernel<<<1, 1, 0, c->stream>>>(c->ctrl, dt, 0.0, 0.0);
-    CPR_CUDA(c, cudaGetLastError());
-    CPR_CUDA(c, stage(c, cpr::MODE_SO1, q, nullptr, c->q1, nullptr, false, c->stream));
-    CPR_CUDA(c, stage(c, cpr::MODE_SO2, c->q1, q, c->q2, nullptr, false, c->stream));
-    cpr::VjpPtrs b2{c->q2, qbar_out, c->adj1, qbar_out, nullptr, nullptr, 2.0 / 3.0, 0.0, 0.0, 2.0 / 3.0 * dt};
+    cpr::VjpPtrs b2{q2, qbar_out, c->adj1, qbar_out, nullptr, nullptr, 2.0 / 3.0, 0.0, 0.0, 2.0 / 3.0 * dt};
     CPR_CUDA(c, vjp(c, b2, c->stream));
-    cpr::VjpPtrs b1{c->q1, c->adj1, c->adj2, c->adj1, nullptr, nullptr, 0.25, 0.0, 0.0, 0.25 * dt};
+    cpr::VjpPtrs b1{q1, c->adj1, c->adj2, c->adj1, nullptr, nullptr, 0.25, 0.0, 0.0, 0.25 * dt};
     CPR_CUDA(c, vjp(c, b1, c->stream));
     cpr::VjpPtrs b0{q, c->adj2, qbar_in, qbar_out, c->adj1, c->adj2, 1.0 / 3.0, 0.75, 1.0, dt};
     CPR_CUDA(c, vjp(c, b0, c->stream));
     return CPR_OK;
+}
+
+// Stage states of one Shu-Osher step of size dt (out = q_next).
+static cpr_status so_stages(cpr_ctx* c, const void* q, void* q1, void* q2, void* q_next, double dt)
+{
+    ctrl_configure_kernel<<<1, 1, 0, c->stream>>>(c->ctrl, dt, 0.0, 0.0);
+    CPR_CUDA(c, cudaGetLastError());
+    CPR_CUDA(c, stage(c, cpr::MODE_SO1, q, nullptr, q1, nullptr, false, c->stream));
+    CPR_CUDA(c, stage(c, cpr::MODE_SO2, q1, q, q2, nullptr, false, c->stream));
+    if (q_next) CPR_CUDA(c, stage(c, cpr::MODE_SO3, q2, q, q_next, nullptr, false, c->stream));
+    return CPR_OK;
+}
+
+// Transpose of one SSP-RK3 step from q with step dt, stages recomputed (in
+// the context's stage buffers).
+extern "C" cpr_status cpr_step_vjp(cpr_ctx* c, const void* q, const void* qbar_out, void* qbar_in, double dt)
+{
+    if (!c) return CPR_EINVAL;
+    if (!q || !qbar_out || !qbar_in) return fail(c, CPR_EINVAL, "q_dev, qbar_out_dev and qbar_in_dev must be non-NULL");
+    if (q == qbar_out || q == qbar_in) return fail(c, CPR_EINVAL, "q_dev must not alias the cotangents");
+    if (!aligned(q) || !aligned(qbar_out) || !aligned(qbar_in))
+        return fail(c, CPR_EINVAL, "state arrays must be 16-byte aligned");
+    cpr_status st = step_adjoint_check(c, dt);
+    if (st != CPR_OK) return st;
+    if ((st = so_stages(c, q, c->q1, c->q2, nullptr, dt)) != CPR_OK) return st;
+    return step_vjp_chain(c, q, c->q1, c->q2, qbar_out, qbar_in, dt);
+}
+
+extern "C" cpr_status cpr_step_stages(cpr_ctx* c, const void* q, void* q1, void* q2, void* q_next, double dt)
+{
+    if (!c) return CPR_EINVAL;
+    if (!q || !q1 || !q2 || !q_next) return fail(c, CPR_EINVAL, "q_dev, q1_dev, q2_dev and q_next_dev must be non-NULL");
+    if (q1 == q || q2 == q || q1 == q2 || q_next == q1 || q_next == q2)
+        return fail(c, CPR_EINVAL, "q1_dev, q2_dev and q_next_dev must not alias q_dev or each other");
+    if (!aligned(q) || !aligned(q1) || !aligned(q2) || !aligned(q_next))
+        return fail(c, CPR_EINVAL, "state arrays must be 16-byte aligned");
+    if (c->cfg.limiter) return fail(c, CPR_EINVAL, "the stage states of an unlimited step only");
+    cpr_status st = step_adjoint_check(c, dt);
+    if (st != CPR_OK) return st;
+    return so_stages(c, q, q1, q2, q_next, dt);
+}
+
+extern "C" cpr_status cpr_step_vjp_stages(cpr_ctx* c, const void* q, const void* q1, const void* q2,
+                                          const void* qbar_out, void* qbar_in, double dt)
+{
+    if (!c) return CPR_EINVAL;
+    if (!q || !q1 || !q2 || !qbar_out || !qbar_in)
+        return fail(c, CPR_EINVAL, "q_dev, q1_dev, q2_dev, qbar_out_dev and qbar_in_dev must be non-NULL");
+    for (const void* x : {q, q1, q2})
+        if (x == qbar_out || x == qbar_in) return fail(c, CPR_EINVAL, "the states must not alias the cotangents");
+    if (!aligned(q) || !aligned(q1) || !aligned(q2) || !aligned(qbar_out) || !aligned(qbar_in))
+        return fail(c, CPR_EINVAL, "state arrays must be 16-byte aligned");
+    cpr_status st = step_adjoint_check(c, dt);
+    if (st != CPR_OK) return st;
+    return step_vjp_chain(c, q, q1, q2, qbar_out, qbar_in, dt);
 }

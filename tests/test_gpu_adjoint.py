@@ -73,6 +73,46 @@ def test_step_vjp_matches_oracle(eqn):
     assert rel(got, ref) <= 1e-12
 
 
+@pytest.mark.parametrize("eqn", [0, 1])
+@pytest.mark.parametrize("dtype", [nat.F64, nat.F32])
+def test_step_stages_and_their_vjp(eqn, dtype):
+    """cpr_step_stages: the stage states and the new state of the Shu-Osher
+    step (Sec. 4) against the oracle's residual composed in that order (FP64
+    <= 1e-12, FP32 <= 1e-5); cpr_step_vjp_stages around them: cpr_step_vjp's
+    result bit for bit (the same transposed residuals around the same stage
+    states) and, in FP64, the oracle's step adjoint to 1e-12; the argument
+    rules."""
+    c, o = make(dtype, eqn=eqn, nx=13, ny=10, p=3, x1=6.5, y1=5.0, ax=0.8, ay=-0.5)
+    q = rough(o, 5)
+    w = np.random.default_rng(6).standard_normal(q.shape)
+    if dtype == nat.F32:
+        q = q.astype(np.float32).astype(np.float64)
+        w = w.astype(np.float32).astype(np.float64)
+    dt = 0.01
+    q1r = q + dt * oracle.residual(o, q)
+    q2r = 0.75 * q + 0.25 * (q1r + dt * oracle.residual(o, q1r))
+    qnr = q / 3.0 + (2.0 / 3.0) * (q2r + dt * oracle.residual(o, q2r))
+    tol = 1e-12 if dtype == nat.F64 else 1e-5
+    with nat.Context(c) as ctx:
+        qd = dev(q, c)
+        q1, q2, qn = (torch.empty_like(qd) for _ in range(3))
+        ctx.step_stages(qd, q1, q2, qn, dt)
+        for got, ref in ((q1, q1r), (q2, q2r), (qn, qnr)):
+            assert rel(got.double().cpu().numpy(), ref) <= tol
+        a = ctx.step_vjp_stages(qd, q1, q2, dev(w, c), dt)
+        b = ctx.step_vjp(qd, dev(w, c), dt)
+        assert torch.equal(a, b)
+        if dtype == nat.F64:
+            assert rel(a.cpu().numpy(), oracle.rk3_vjp(o, q, dt, w)) <= 1e-12
+        wd = dev(w, c)
+        for bad in ((qd, qd, q2, qn, dt), (qd, q1, q1, qn, dt), (qd, q1, q2, q2, dt), (qd, q1, q2, qn, 0.0)):
+            with pytest.raises(nat.CprError):
+                ctx.step_stages(*bad)
+        for bad in ((qd, q1, q2, qd, dt), (qd, q1, wd, wd, dt), (qd, q1, q2, wd, float("nan"))):
+            with pytest.raises(nat.CprError):
+                ctx.step_vjp_stages(*bad, qbar_in=torch.empty_like(qd))
+
+
 def test_vjp_dot_product_with_gpu_residual_differences():
     c, o = make(nat.F64, eqn=1, nx=10, ny=12, p=2, x1=5.0, y1=6.0, bc_x=1)
     q = dev(rough(o, 5), c)
