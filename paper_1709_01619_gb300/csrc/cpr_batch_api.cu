@@ -215,10 +215,6 @@ cudaError_t ensure_inst_streams(cpr_batch* b)
     return e;
 }
 
-// Enqueue on s (which must be capturing) `steps` RK3 steps of every instance
-// as independent chains: fork from s, one stream per instance, join back.
-// timing != 0: only stages 1 and 2 with swap 0 (they leave the caller's
-// states, the low parts and the time control untouched), for the autotuner.
 // `steps` RK3 steps of instance i on stream si (the increment form's high
 // part alternating between the caller's array and Y, starting in the
 // caller's); timing: stages 1 and 2 only, as below.
@@ -243,6 +239,10 @@ cudaError_t enqueue_inst_steps(cpr_batch* b, int i, int steps, cudaStream_t si, 
     return e;
 }
 
+// Enqueue on s (which must be capturing) `steps` RK3 steps of every instance
+// as independent chains: fork from s, one stream per instance, join back.
+// timing != 0: only stages 1 and 2 with swap 0 (they leave the caller's
+// states, the low parts and the time control untouched), for the autotuner.
 cudaError_t enqueue_inst_chains(cpr_batch* b, int steps, cudaStream_t s, bool timing)
 {
     cudaError_t e = cudaEventRecord(b->fork_ev, s);
@@ -643,7 +643,7 @@ static cpr_status batch_begin(cpr_batch* b, void* const* q, int nsteps, double d
 // then `steps` steps (head); or `steps` steps, the copy back of a state left
 // in Y and the copy of the state out (q_out) (tail).  The instance states are
 // the bound arrays (x_cached).
-static cudaError_t capture_host_graph(cpr_batch* b, bool head, const void* const* q_in, void* const* q_out,
+static cudaError_t capture_chain_graph(cpr_batch* b, bool head, const void* const* q_in, void* const* q_out,
                                       int steps, bool cfl, cudaGraphExec_t* exec)
 {
     const size_t esize = b->dtype == CPR_F32 ? 4 : 8;
@@ -737,7 +737,7 @@ static cpr_status run_chains(cpr_batch* b, int nsteps, double dt_fixed, const vo
             if (b->gh_head) cudaGraphExecDestroy(b->gh_head);
             b->gh_head = nullptr;
             b->gh_in.clear();
-            BATCH_CUDA(b, capture_host_graph(b, true, q_in, q_out, K, cfl != 0, &b->gh_head));
+            BATCH_CUDA(b, capture_chain_graph(b, true, q_in, q_out, K, cfl != 0, &b->gh_head));
             b->gh_in.assign(q_in, q_in + b->n);
             b->gh_cfl = cfl;
         }
@@ -745,7 +745,7 @@ static cpr_status run_chains(cpr_batch* b, int nsteps, double dt_fixed, const vo
             if (b->gh_tail) cudaGraphExecDestroy(b->gh_tail);
             b->gh_tail = nullptr;
             b->gh_out.clear();
-            BATCH_CUDA(b, capture_host_graph(b, false, q_in, q_out, tail, cfl != 0, &b->gh_tail));
+            BATCH_CUDA(b, capture_chain_graph(b, false, q_in, q_out, tail, cfl != 0, &b->gh_tail));
             b->gh_out.assign(q_out, q_out + b->n);
             b->gh_tail_steps = tail;
         }
@@ -753,13 +753,13 @@ static cpr_status run_chains(cpr_batch* b, int nsteps, double dt_fixed, const vo
         if (!b->gd_head || b->gd_cfl != cfl) {
             if (b->gd_head) cudaGraphExecDestroy(b->gd_head);
             b->gd_head = nullptr;
-            BATCH_CUDA(b, capture_host_graph(b, true, nullptr, nullptr, K, cfl != 0, &b->gd_head));
+            BATCH_CUDA(b, capture_chain_graph(b, true, nullptr, nullptr, K, cfl != 0, &b->gd_head));
             b->gd_cfl = cfl;
         }
         if (!b->gd_tail || b->gd_tail_steps != tail) {
             if (b->gd_tail) cudaGraphExecDestroy(b->gd_tail);
             b->gd_tail = nullptr;
-            BATCH_CUDA(b, capture_host_graph(b, false, nullptr, nullptr, tail, cfl != 0, &b->gd_tail));
+            BATCH_CUDA(b, capture_chain_graph(b, false, nullptr, nullptr, tail, cfl != 0, &b->gd_tail));
             b->gd_tail_steps = tail;
         }
     }
