@@ -91,6 +91,9 @@ def test_null_arguments(lib):
     assert lib.cpr_residual(None, None, None) == _native.CPR_EINVAL
     assert lib.cpr_step(None, None, 1, 0.0, 0.0) == _native.CPR_EINVAL
     assert lib.cpr_norms(None, None, None, None) == _native.CPR_EINVAL
+    assert lib.cpr_step_vjp(None, None, None, None, 0.1) == _native.CPR_EINVAL
+    assert lib.cpr_step_stages(None, None, None, None, None, 0.1) == _native.CPR_EINVAL
+    assert lib.cpr_step_vjp_stages(None, None, None, None, None, None, 0.1) == _native.CPR_EINVAL
     assert lib.cpr_state_elems(None) == 0
     lib.cpr_destroy(None)
 
