@@ -8,6 +8,12 @@
 #include "cpr_stage.cuh"
 #include "cpr_adjoint.cuh"
 
+// Small-tile FP64 stage kernel for grids of at most one tile per two SMs
+// (0: off).
+#ifndef CPR_STAGE_SMALL
+#define CPR_STAGE_SMALL 1
+#endif
+
 namespace cpr {
 
 
@@ -30,13 +36,37 @@ static cudaError_t stage_one(const LaunchCfg& c, const StageArgs<T>& A, int ctas
     // CTAs per SM the wide instantiation is compiled for: the grid fits the
     // device at once up to that many per SM
     constexpr int WIDE_PER_SM = stage_min_blocks<T, N, true, TX * TY>();
+    // and, in FP64, tiles of 4 x 4 elements for grids of at most one tile per
+    // two SMs: four times the CTAs, so that more SMs share the FP64 work of a
+    // grid that would leave most of them idle (Euler, LP divergence, Rusanov
+    // flux; 24^2 p = 3 192.6 -> 109.9 ms for 1003 steps, 64^2 514 -> 317 ms;
+    // at 96^2, 144 tiles, slower: 773 -> 807 ms; in FP32 slower at every size,
+    // 24^2 17.1 -> 17.5 ms, 96^2 70.5 -> 78.9 ms)
+    constexpr bool HAS_SMALL = sizeof(T) == 8 && EQ == EQ_EULER && DIV == DIV_LP && FLUX == FLUX_RUSANOV &&
+                               CPR_STAGE_SMALL != 0;
+    constexpr int SX = 4, SY = 4;
+    [[maybe_unused]] const size_t smem_s = sizeof(T) * StageLayout<N, V, SX, SY, stage_delta<T>()>::TOTAL;
     if (prep) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess && HAS_PF)
             e = cudaFuncSetAttribute(kern_pf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess && HAS_WIDE)
             e = cudaFuncSetAttribute(kern_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if constexpr (HAS_SMALL)
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(cpr_stage_kernel<T, P, EQ, DIV, FLUX, SX, SY, stage_delta<T>(), false, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s);
         return e;
+    }
+    if constexpr (HAS_SMALL) {
+        if (c.sms > 0 && 2 * ctas <= c.sms) {
+            StageArgs<T> As = A;
+            As.tiles_x = (c.nx + SX - 1) / SX;
+            const int grid = As.tiles_x * ((c.ny + SY - 1) / SY);
+            cpr_stage_kernel<T, P, EQ, DIV, FLUX, SX, SY, stage_delta<T>(), false, true>
+                <<<grid, SX * SY * N, smem_s, s>>>(As);
+            return cudaGetLastError();
+        }
     }
     if (HAS_PF && A.pf_lo) kern_pf<<<ctas, NT, smem, s>>>(A);
     else if (HAS_WIDE && c.sms > 0 && ctas <= WIDE_PER_SM * c.sms) kern_w<<<ctas, NT, smem, s>>>(A);
