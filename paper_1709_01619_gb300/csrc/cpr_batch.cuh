@@ -110,6 +110,7 @@ template <class T, int P, int EQ, int DIV, int FLUX, int TX, int TY, bool DELTA,
 __global__ void __launch_bounds__(TX * TY * (P + 1), (batch_min_blocks<T, P + 1>()))
 cpr_batch_stage_kernel(const BatchArgs<T> B)
 {
+    static_assert((TX * TY * (P + 1)) % 32 == 0, "whole warps: the warp-level reductions use every lane");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // The work item's arguments live in shared memory, read at their points
     // of use instead of occupying registers through the whole tile.

@@ -909,6 +909,7 @@ template <class T, int P, int EQ, int DIV, int FLUX, int TX, int TY, bool DELTA,
 __global__ void __launch_bounds__(TX * TY * (P + 1), (stage_min_blocks<T, P + 1, WIDE, TX * TY>()))
 cpr_stage_kernel(const StageArgs<T> A)
 {
+    static_assert((TX * TY * (P + 1)) % 32 == 0, "whole warps: the warp-level reductions use every lane");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     stage_tile<T, P, EQ, DIV, FLUX, TX, TY, DELTA, PF>(A, A.tab, A.tp, blockIdx.x, threadIdx.x, smem_raw,
                                                        gridDim.x);

@@ -42,9 +42,10 @@ static cudaError_t stage_one(const LaunchCfg& c, const StageArgs<T>& A, int ctas
     // flux; 24^2 p = 3 192.6 -> 109.9 ms for 1003 steps, 64^2 514 -> 317 ms;
     // at 96^2, 144 tiles, slower: 773 -> 807 ms; in FP32 slower at every size,
     // 24^2 17.1 -> 17.5 ms, 96^2 70.5 -> 78.9 ms)
-    constexpr bool HAS_SMALL = sizeof(T) == 8 && EQ == EQ_EULER && DIV == DIV_LP && FLUX == FLUX_RUSANOV &&
-                               CPR_STAGE_SMALL != 0;
+    // (whole warps only: p = 1 and 3, 32 and 64 threads)
     constexpr int SX = 4, SY = 4;
+    constexpr bool HAS_SMALL = sizeof(T) == 8 && EQ == EQ_EULER && DIV == DIV_LP && FLUX == FLUX_RUSANOV &&
+                               (SX * SY * N) % 32 == 0 && CPR_STAGE_SMALL != 0;
     [[maybe_unused]] const size_t smem_s = sizeof(T) * StageLayout<N, V, SX, SY, stage_delta<T>()>::TOTAL;
     if (prep) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
