@@ -69,12 +69,6 @@ MOVED_ARRAYS_PER_STEP = 10
 # replayed cold (writes stay in L2) and the 1024^2 case.
 NCU_TRAFFIC_128 = 8.429e6
 NCU_TRAFFIC_1024 = 8.575e8
-# The headline batch: DRAM bytes per batch stage (the 64 instances' stage
-# launches of three RK3 steps, replayed one at a time with cold caches,
-# divided by the 9 stages): reads 893.9 MB, the 6 input arrays per RK3 step
-# of the increment form, writes 4.3 MB (the results stay in L2 at the end of
-# each replayed launch) (profiles/launches_batch64_fp32.md).
-NCU_TRAFFIC_BATCH_STAGE = 8.982e8
 FALLBACK_HBM_GBS = 6800.0
 # FP64 floating-point operations per DOF-stage of the Euler LP stage at
 # p = 3: the method's own count (point fluxes about 25, the two line
@@ -437,7 +431,7 @@ def batch_headline(args, world, local, peak):
         t_min=min(t_reached), t_max=max(t_reached), e2e=e2e, e2e_equal=e2e_equal, state_bytes=state_bytes,
         tuned=[{"p": p, "family": f, "grid": g} for p, f, g in choices], per_instance=per_inst,
         roofline={"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                  "traffic": NCU_TRAFFIC_BATCH_STAGE, "unit_of_work": "one batch stage (all 64 instances)",
+                  "traffic": None, "unit_of_work": "one batch stage (all 64 instances)",
                   "bytes_per_stage": bytes_per_stage, "stage_ms": stage_ms,
                   "moved_frac": achieved * MOVED_ARRAYS_PER_STEP / ALGO_ARRAYS_PER_STEP / peak,
                   "kernel": "cpr_stage_kernel<float,p,Euler,LP,Rusanov> (p = 2, 3, 4)"},
